@@ -1,0 +1,160 @@
+/*
+ * parquet.h -- C ABI of the GB300 parquet solver.
+ *
+ * One context holds one parquet solve of the single-band Hubbard model
+ * (Li, Wentzell, Pudleiner, Thunstroem, Held, arXiv:1510.03330) on one GPU:
+ * the reducible vertices Phi_r (r = d, m, s, t) on the frequency box, the
+ * self-energy Sigma on the extended fermionic range, and the scratch of one
+ * iteration.  pq_iterate runs the paper's self-consistent loop (Sec. II):
+ * Dyson equation (App. A, Eq. PA_Dyson), bubbles, kernel functions K1/K2
+ * (Sec. II.A), parquet equations with the kernel fill (Eq. PA_F, App. A Eqs.
+ * PA_Gamma_dm, PA_Gamma_st), the Bethe-Salpeter equations (Eq. PA_F_Phi),
+ * the high-frequency regulated Schwinger-Dyson self-energy (Sec. II.B,
+ * Eq. PA_Sigma) and linear mixing.
+ *
+ * Conventions shared by every call:
+ *   - complex numbers are (re, im) pairs of doubles, "c128" below;
+ *   - k = (k-vector, n) with n fastest: index ik*Nnu + (n - n_lo),
+ *     n_lo = -Nnu/2; Q = (q-vector, m): index iq*NOmega + (m - m_lo),
+ *     m_lo = -floor(NOmega/2); ik = ix*L + iy for k = 2 pi (ix, iy)/L;
+ *   - Sigma is stored on the extended range e in [m_lo+n_lo, m_hi+n_hi]
+ *     (NOmega+Nnu-1 frequencies), index ik*n_ext + (e - e_lo);
+ *   - every host buffer is owned by the caller; the library copies from or
+ *     into it before returning and keeps no pointer to it;
+ *   - device memory is owned by the context: allocated in pq_init (through
+ *     the caller's allocator if one is given) and released in pq_destroy;
+ *   - no call throws; each returns a pq_status and pq_last_error() gives the
+ *     message of the last failure on that context;
+ *   - one context is used from one host thread at a time; its kernels run
+ *     on the stream given in pq_options (the legacy default stream if NULL).
+ */
+#ifndef PARQUET_GB300_H
+#define PARQUET_GB300_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define PQ_API __attribute__((visibility("default")))
+#else
+#define PQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pq_ctx pq_ctx;
+
+typedef enum {
+  PQ_OK = 0,
+  PQ_EINVAL = 1,   /* bad argument or size; nothing changed */
+  PQ_ENOMEM = 2,   /* device allocation failed; the message gives the bytes */
+  PQ_ECUDA = 3,    /* a CUDA call failed; the context is poisoned */
+  PQ_ENOTCONV = 4, /* pq_iterate reached max_iter above tol (state is valid) */
+  PQ_ETIMEOUT = 5, /* reserved: a bounded device wait gave up */
+  PQ_ENAN = 6,     /* a non-finite Sigma appeared; the context is poisoned */
+  PQ_ESTATE = 7    /* the context is poisoned by an earlier PQ_ECUDA/PQ_ENAN */
+} pq_status;
+
+typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
+
+/* Arithmetic of the vertex storage and the BSE products.
+ * PQ_FP64: complex128 vertices, FP64 everywhere.
+ * PQ_SPLIT_*: complex64 vertices; the BSE runs on the tensor cores as a
+ * split-operand product with FP32 accumulation; Dyson, K1/K2, Sigma stay FP64. */
+typedef enum {
+  PQ_FP64 = 0,
+  PQ_SPLIT_TF32X3 = 1,
+  PQ_SPLIT_BF16X3 = 2,
+  PQ_SPLIT_BF16X6 = 3
+} pq_precision;
+
+typedef struct {
+  int precision;          /* pq_precision; default PQ_FP64 */
+  double mix_alpha;       /* weight of the new iterate in linear mixing; default 0.5 */
+  int sigma2_box_factor;  /* kernel-term box / vertex box (Sec. II.B); default 3 */
+  double hop;             /* t (square) or half-bandwidth D (Bethe); default 1 */
+  int tau_panels;         /* Gauss-Legendre panels on [0, beta] for Sigma~1; default 64 */
+  int tau_order;          /* nodes per panel; default 16 */
+  int tau_matsubara;      /* Matsubara cut M of G(tau): n in [-M, M-1]; default 2048 */
+  int time_steps;         /* nonzero: record per-step CUDA-event times (pq_step_times) */
+  void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
+  /* Optional device allocator: returns 256-byte aligned device memory or NULL.
+   * When NULL, cudaMalloc/cudaFree are used. */
+  void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+  void (*dev_free)(void *ptr, size_t bytes, void *alloc_ctx);
+  void *alloc_ctx;
+} pq_options;
+
+/* Fill *opt with the defaults listed above. */
+PQ_API void pq_default_options(pq_options *opt);
+
+/* Create a solve.  lattice: pq_lattice; beta > 0; L >= 1 (L = 1 for Bethe);
+ * n_nu even >= 2; n_Omega >= 1.  Allocates all device memory (PQ_ENOMEM with
+ * the byte count if it does not fit) and sets Phi = 0, Sigma = 0 and
+ * Lambda = (U, -U, 2U, 0), the parquet approximation (Sec. II.A).
+ * opt may be NULL for the defaults.  On success *out owns the context. */
+PQ_API pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, int L,
+                  int n_nu, int n_Omega, const pq_options *opt);
+
+/* Fully irreducible vertex of one channel (0..3 = d, m, s, t), local in
+ * momentum, tabulated on |n|, |n'|, |m| <= n_lambda as host c128
+ * [2n_lambda+1 (m)][2n_lambda (n)][2n_lambda (n')] with n in
+ * [-n_lambda, n_lambda-1] and m in [-n_lambda, n_lambda]; outside the table
+ * the channel keeps its parquet-approximation value (Sec. III.A, "extend
+ * Lambda ... by supplementing it with the lowest order values").
+ * Not available in this build: returns PQ_EINVAL. */
+PQ_API pq_status pq_set_Lambda(pq_ctx *ctx, int channel, const double *host_c128, int n_lambda);
+
+/* Run up to max_iter iterations; stop after the first one whose
+ * max_k |Sigma_new(k) - Sigma(k)| < tol.  Writes the count done and the last
+ * max |dSigma| when the pointers are non-NULL.  PQ_ENOTCONV if tol was not
+ * reached (the state is still valid).  One device->host read of one scalar
+ * per iteration. */
+PQ_API pq_status pq_iterate(pq_ctx *ctx, int max_iter, double tol, int *iters_done,
+                     double *last_max_dsigma);
+
+/* Self-energy of the current state, host c128 [L*L][n_ext]; len = number of
+ * doubles available in out (>= 2*L*L*n_ext). */
+PQ_API pq_status pq_get_Sigma(const pq_ctx *ctx, double *out, size_t len);
+
+/* Full vertex F_r(Q) of the last iteration (the one assembled from the state
+ * that iteration started from), host c128 [n][n], n = L*L*Nnu. */
+PQ_API pq_status pq_get_F(const pq_ctx *ctx, int channel, int Q, double *out, size_t len);
+
+/* Reducible vertex Phi_r(Q) of the current state, host c128 [n][n]. */
+PQ_API pq_status pq_get_Phi(const pq_ctx *ctx, int channel, int Q, double *out, size_t len);
+
+/* Susceptibility of the last iteration, host c128 [N_Q]:
+ * chi_r(Q) = -sum_k X_r(Q,k) - sum_{k,k'} X_r(Q,k) F_r^{k,k'}(Q) X_r(Q,k'),
+ * X_ph = (T/N) G(k)G(k+q) for d, m and X_pp = (T/N) G(k)G(q-k) for s, t
+ * (App. A, "Notations": chi from F and the bare bubble). */
+PQ_API pq_status pq_get_chi(const pq_ctx *ctx, int channel, double *out, size_t len);
+
+/* Replace the state: Phi as host c128 [4][N_Q][n][n] (converted to the
+ * storage precision) and Sigma as host c128 [L*L][n_ext]; either may be NULL
+ * to keep it. */
+PQ_API pq_status pq_set_state(pq_ctx *ctx, const double *phi_c128, const double *sigma_c128);
+
+/* Sizes: out[0..7] = L*L, n, N_Q, n_ext, Nnu, NOmega, bytes of device memory
+ * held, storage bytes per complex vertex element. */
+PQ_API pq_status pq_get_sizes(const pq_ctx *ctx, long long *out8);
+
+/* Per-step device times (ms) of the last iteration, when time_steps was set:
+ * out[0..PQ_NSTEPS-1] in the order of pq_step_name(i). */
+#define PQ_NSTEPS 9
+PQ_API pq_status pq_step_times(const pq_ctx *ctx, float *out, int n);
+PQ_API const char *pq_step_name(int i);
+
+/* Message of the last failure on ctx (or of the last failed pq_init when
+ * ctx is NULL). */
+PQ_API const char *pq_last_error(const pq_ctx *ctx);
+
+/* Release the context and its device memory.  NULL is a no-op. */
+PQ_API void pq_destroy(pq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARQUET_GB300_H */

@@ -1,0 +1,515 @@
+// C ABI of the GB300 parquet solver (include/parquet.h): context life cycle,
+// device memory, and the iteration driver that sequences the steps of one
+// self-consistent parquet iteration (Sec. II) on one stream.
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <initializer_list>
+#include <string>
+#include <vector>
+
+#include "../../include/parquet.h"
+#include "pq_common.cuh"
+#include "pq_internal.h"
+
+using pq::Buffers;
+using pq::Grid;
+using pq::Sizes;
+
+struct pq_ctx {
+  Grid g{};
+  Sizes z{};
+  pq_options opt{};
+  Buffers b{};
+  cudaStream_t st = nullptr;
+  bool c64 = false;
+  bool poisoned = false;
+  double lam[8] = {0};
+  std::vector<std::pair<void *, size_t>> allocs;
+  size_t bytes = 0;
+  std::string err;
+  cudaEvent_t ev[PQ_NSTEPS + 1] = {};
+  float times[PQ_NSTEPS] = {0};
+  int iterations = 0;
+};
+
+namespace {
+
+std::string g_init_err;
+
+const char *kStepNames[PQ_NSTEPS] = {"dyson",    "bubbles",      "kernels", "sigma1", "sigma2",
+                                     "assemble", "sigma_update", "bse",     "total"};
+
+pq_status fail(pq_ctx *c, pq_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == PQ_ECUDA || s == PQ_ENAN) c->poisoned = true;
+  } else {
+    g_init_err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, PQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void *dalloc(pq_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *p = nullptr;
+  if (c->opt.dev_alloc) {
+    p = c->opt.dev_alloc(bytes, c->opt.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->allocs.push_back({p, bytes});
+    c->bytes += bytes;
+  }
+  return p;
+}
+
+void release_all(pq_ctx *c) {
+  for (auto &a : c->allocs) {
+    if (c->opt.dev_free)
+      c->opt.dev_free(a.first, a.second, c->opt.alloc_ctx);
+    else
+      cudaFree(a.first);
+  }
+  c->allocs.clear();
+  c->bytes = 0;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_p.
+void gauss_legendre(int p, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(p, 0.0);
+  w.assign(p, 0.0);
+  for (int i = 0; i < p; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (p + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= p; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      if (p == 1) {
+        p1 = z;
+        p0 = 1.0;
+      }
+      dp = p * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    x[p - 1 - i] = z;
+    w[p - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+size_t vbytes(const pq_ctx *c) {
+  return (size_t)4 * c->g.nQ * (size_t)c->g.n * c->g.n * (c->c64 ? sizeof(float2) : sizeof(double2));
+}
+
+__global__ void phi_from_c128(float2 *dst, const double2 *src, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+pq_status run_iteration(pq_ctx *c, double *dmax) {
+  cudaStream_t st = c->st;
+  Grid &g = c->g;
+  Buffers &b = c->b;
+  const bool tm = c->opt.time_steps != 0;
+  auto mark = [&](int i) {
+    if (tm) cudaEventRecord(c->ev[i], st);
+  };
+  mark(0);
+  CK(pq::launch_tail_and_green(st, g, b));
+  mark(1);
+  CK(pq::launch_bubbles(st, g, b));
+  mark(2);
+  CK(pq::launch_kernels_extract(st, g, b, c->c64));
+  mark(3);
+  CK(pq::launch_sigma1(st, g, c->z, b));
+  mark(4);
+  CK(pq::launch_sigma2(st, g, c->z, b));
+  mark(5);
+  CK(pq::launch_assemble(st, g, b, c->c64, c->lam));
+  mark(6);
+  CK(pq::launch_sigma_update(st, g, b));
+  mark(7);
+  const long long nn = g.n;
+  if (!c->c64) {
+    CK(pq::zgemm_fp64(st, g.n, g.n, g.n, make_double2(g.mix, 0.0), (const double2 *)b.gam, g.n, nn * nn,
+                      (const double2 *)b.fv, g.n, nn * nn, make_double2(1.0 - g.mix, 0.0), (double2 *)b.phi, g.n,
+                      nn * nn, 4 * g.nQ));
+  } else {
+    return fail(c, PQ_EINVAL, "split-precision BSE not available in this build");
+  }
+  mark(8);
+  double h[3];
+  CK(cudaMemcpyAsync(h, b.scal, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (tm) {
+    for (int i = 0; i < PQ_NSTEPS - 1; ++i) cudaEventElapsedTime(&c->times[i], c->ev[i], c->ev[i + 1]);
+    cudaEventElapsedTime(&c->times[PQ_NSTEPS - 1], c->ev[0], c->ev[PQ_NSTEPS - 1]);
+  }
+  if (h[2] != 0.0 || !std::isfinite(h[1])) return fail(c, PQ_ENAN, "non-finite self-energy after iteration");
+  *dmax = h[1];
+  c->iterations++;
+  return PQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pq_default_options(pq_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = PQ_FP64;
+  o->mix_alpha = 0.5;
+  o->sigma2_box_factor = 3;
+  o->hop = 1.0;
+  o->tau_panels = 64;
+  o->tau_order = 16;
+  o->tau_matsubara = 2048;
+}
+
+pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, int L, int n_nu, int n_Omega,
+                  const pq_options *opt) {
+  if (!out) return fail(nullptr, PQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  pq_options o;
+  pq_default_options(&o);
+  if (opt) o = *opt;
+  if (lattice != PQ_BETHE && lattice != PQ_SQUARE) return fail(nullptr, PQ_EINVAL, "unknown lattice %d", lattice);
+  if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, PQ_EINVAL, "beta must be positive");
+  if (L < 1 || (lattice == PQ_BETHE && L != 1)) return fail(nullptr, PQ_EINVAL, "L must be >= 1 (1 for Bethe)");
+  if (n_nu < 2 || n_nu % 2) return fail(nullptr, PQ_EINVAL, "n_nu must be even and >= 2");
+  if (n_Omega < 1) return fail(nullptr, PQ_EINVAL, "n_Omega must be >= 1");
+  if (o.sigma2_box_factor < 1) return fail(nullptr, PQ_EINVAL, "sigma2_box_factor must be >= 1");
+  if (o.tau_panels < 1 || o.tau_order < 2 || o.tau_matsubara < 1)
+    return fail(nullptr, PQ_EINVAL, "bad imaginary-time quadrature sizes");
+  if (o.precision < PQ_FP64 || o.precision > PQ_SPLIT_BF16X6) return fail(nullptr, PQ_EINVAL, "unknown precision");
+  if (!(o.mix_alpha > 0.0 && o.mix_alpha <= 1.0)) return fail(nullptr, PQ_EINVAL, "mix_alpha must be in (0, 1]");
+  if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+    return fail(nullptr, PQ_EINVAL, "dev_alloc and dev_free must be given together");
+
+  pq_ctx *c = new pq_ctx();
+  c->opt = o;
+  c->st = (cudaStream_t)o.cuda_stream;
+  c->c64 = (o.precision != PQ_FP64);
+  Grid &g = c->g;
+  g.lattice = lattice;
+  g.L = L;
+  g.nk = L * L;
+  g.n_nu = n_nu;
+  g.n_om = n_Omega;
+  g.n = g.nk * n_nu;
+  g.nQ = g.nk * n_Omega;
+  g.n_ext = n_Omega + n_nu - 1;
+  g.n_lo = -n_nu / 2;
+  g.n_hi = n_nu / 2 - 1;
+  g.m_lo = -(n_Omega / 2);
+  g.m_hi = g.m_lo + n_Omega - 1;
+  g.e_lo = g.m_lo + g.n_lo;
+  g.e_hi = g.m_hi + g.n_hi;
+  const int f = o.sigma2_box_factor;
+  g.bf_lo = -(f * n_nu) / 2;
+  g.bf_hi = (f * n_nu) / 2 - 1;
+  g.bb_lo = -((f * n_Omega) / 2);
+  g.bb_hi = g.bb_lo + f * n_Omega - 1;
+  g.beta = beta;
+  g.T = 1.0 / beta;
+  g.U = U;
+  g.mu = mu;
+  g.hop = o.hop;
+  g.mix = o.mix_alpha;
+  // frequency range of the Sigma~2 bubble tables and of the G table
+  Sizes &z = c->z;
+  int j_lo = std::min(std::min(g.bf_lo, g.e_lo + g.bb_lo), g.bb_lo - g.e_hi - 1 - g.m_hi);
+  int j_hi = std::max(std::max(g.bf_hi, g.e_hi + g.bb_hi), g.bb_hi - g.e_lo - 1 - g.m_lo);
+  z.j_lo = j_lo;
+  z.nj = j_hi - j_lo + 1;
+  int lo = std::min({j_lo, j_lo + g.m_lo, g.m_lo - j_hi - 1, g.e_lo + g.m_lo, g.m_lo - g.e_hi - 1, g.e_lo + g.bb_lo});
+  int hi = std::max({j_hi, j_hi + g.m_hi, g.m_hi - j_lo - 1, g.e_hi + g.m_hi, g.m_hi - g.e_lo - 1, g.e_hi + g.bb_hi});
+  g.g_lo = lo;
+  g.n_g = hi - lo + 1;
+  z.M = o.tau_matsubara;
+  z.ntau = o.tau_panels * o.tau_order;
+  c->lam[0] = U;
+  c->lam[2] = -U;
+  c->lam[4] = 2.0 * U;
+  c->lam[6] = 0.0;
+
+  if (pq::assemble_smem_bytes(g, c->c64) > 200 * 1024) {
+    delete c;
+    return fail(nullptr, PQ_EINVAL, "NOmega*Nnu = %d too large for one vertex block in shared memory",
+                n_Omega * n_nu);
+  }
+
+  // device memory
+  const size_t vb = vbytes(c);
+  const size_t cs = sizeof(double2);
+  Buffers &b = c->b;
+  struct Req {
+    void **p;
+    size_t bytes;
+  } reqs[] = {
+      {&b.phi, vb},
+      {&b.gam, vb},
+      {&b.fv, vb},
+      {(void **)&b.sigma, cs * g.nk * g.n_ext},
+      {(void **)&b.sigma_new, cs * g.nk * g.n_ext},
+      {(void **)&b.sigma1, cs * g.nk * g.n_ext},
+      {(void **)&b.sigma2, cs * g.nk * g.n_ext},
+      {(void **)&b.gtab, cs * g.nk * g.n_g},
+      {(void **)&b.xph, cs * g.nQ * (size_t)g.n},
+      {(void **)&b.xpp, cs * g.nQ * (size_t)g.n},
+      {(void **)&b.k1, cs * 4 * g.nQ},
+      {(void **)&b.k2row, cs * 4 * (size_t)g.n * g.nQ},
+      {(void **)&b.k2col, cs * 4 * (size_t)g.n * g.nQ},
+      {(void **)&b.dfpart, cs * (size_t)g.n * g.nk},
+      {(void **)&b.scal, 8 * sizeof(double)},
+      {(void **)&b.s1_R, cs * g.nk * 2 * (size_t)z.M},
+      {(void **)&b.s1_E, cs * 2 * (size_t)z.M * z.ntau},
+      {(void **)&b.s1_Ef, cs * (size_t)z.ntau * g.n_ext},
+      {(void **)&b.s1_ph, cs * g.nk * g.nk},
+      {(void **)&b.s1_phc, cs * g.nk * g.nk},
+      {(void **)&b.s1_gkt, cs * g.nk * (size_t)z.ntau},
+      {(void **)&b.s1_grt, cs * g.nk * (size_t)z.ntau},
+      {(void **)&b.s1_srn, cs * g.nk * g.n_ext},
+      {(void **)&b.s1_tau, sizeof(double) * z.ntau},
+      {(void **)&b.s2_bph, cs * g.nQ * (size_t)z.nj},
+      {(void **)&b.s2_bpp, cs * g.nQ * (size_t)z.nj},
+      {(void **)&b.s2_cph, cs * 2 * g.nQ * (size_t)n_nu},
+      {(void **)&b.s2_cpp, cs * g.nQ * (size_t)n_nu},
+      {(void **)&b.chi, cs * 4 * g.nQ},
+  };
+  size_t need = 0;
+  for (auto &r : reqs) need += (r.bytes + 255) & ~(size_t)255;
+  for (auto &r : reqs) {
+    *r.p = dalloc(c, r.bytes);
+    if (!*r.p) {
+      release_all(c);
+      delete c;
+      return fail(nullptr, PQ_ENOMEM, "device allocation failed: the solve needs %zu bytes", need);
+    }
+  }
+
+  // imaginary-time quadrature and transforms of Sigma~1
+  std::vector<double> gx, gw;
+  gauss_legendre(o.tau_order, gx, gw);
+  std::vector<double> tau(z.ntau), wt(z.ntau);
+  const double h = beta / o.tau_panels;
+  for (int p = 0; p < o.tau_panels; ++p)
+    for (int i = 0; i < o.tau_order; ++i) {
+      tau[p * o.tau_order + i] = p * h + 0.5 * h * (gx[i] + 1.0);
+      wt[p * o.tau_order + i] = 0.5 * h * gw[i];
+    }
+  std::vector<std::complex<double>> E((size_t)2 * z.M * z.ntau), Ef((size_t)z.ntau * g.n_ext);
+  for (int i = 0; i < 2 * z.M; ++i) {
+    double nu = (2.0 * (i - z.M) + 1.0) * M_PI / beta;
+    for (int j = 0; j < z.ntau; ++j) E[(size_t)i * z.ntau + j] = std::exp(std::complex<double>(0.0, -nu * tau[j]));
+  }
+  for (int j = 0; j < z.ntau; ++j)
+    for (int e = 0; e < g.n_ext; ++e) {
+      double nu = (2.0 * (g.e_lo + e) + 1.0) * M_PI / beta;
+      Ef[(size_t)j * g.n_ext + e] = wt[j] * std::exp(std::complex<double>(0.0, nu * tau[j]));
+    }
+  std::vector<std::complex<double>> ph((size_t)g.nk * g.nk), phc((size_t)g.nk * g.nk);
+  for (int r = 0; r < g.nk; ++r)
+    for (int k = 0; k < g.nk; ++k) {
+      double arg = 2.0 * M_PI * ((double)(r / L) * (k / L) + (double)(r % L) * (k % L)) / L;
+      ph[(size_t)r * g.nk + k] = std::exp(std::complex<double>(0.0, arg)) / (double)g.nk;
+      phc[(size_t)k * g.nk + r] = std::exp(std::complex<double>(0.0, -arg));
+    }
+  pq_status s = PQ_OK;
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    if (s == PQ_OK && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      s = fail(c, PQ_ECUDA, "upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+  };
+  up(b.s1_E, E.data(), E.size() * cs);
+  up(b.s1_Ef, Ef.data(), Ef.size() * cs);
+  up(b.s1_ph, ph.data(), ph.size() * cs);
+  up(b.s1_phc, phc.data(), phc.size() * cs);
+  up(b.s1_tau, tau.data(), tau.size() * sizeof(double));
+  if (s == PQ_OK) {
+    cudaError_t e1 = cudaMemset(b.phi, 0, vb);
+    cudaError_t e2 = cudaMemset(b.sigma, 0, cs * g.nk * g.n_ext);
+    cudaError_t e3 = cudaMemset(b.scal, 0, 8 * sizeof(double));
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) s = fail(c, PQ_ECUDA, "memset failed");
+  }
+  for (int i = 0; s == PQ_OK && i <= PQ_NSTEPS; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) s = fail(c, PQ_ECUDA, "event create failed");
+  if (s != PQ_OK) {
+    g_init_err = c->err;
+    pq_destroy(c);
+    return s;
+  }
+  *out = c;
+  return PQ_OK;
+}
+
+pq_status pq_set_Lambda(pq_ctx *c, int channel, const double *host_c128, int n_lambda) {
+  (void)channel;
+  (void)host_c128;
+  (void)n_lambda;
+  if (!c) return PQ_EINVAL;
+  return fail(c, PQ_EINVAL, "a tabulated Lambda is not available in this build; the parquet approximation is used");
+}
+
+pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, double *last) {
+  if (!c) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned by an earlier error: %s", c->err.c_str());
+  if (max_iter < 0) return fail(c, PQ_EINVAL, "max_iter < 0");
+  double d = INFINITY;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    pq_status s = run_iteration(c, &d);
+    if (s != PQ_OK) {
+      if (iters_done) *iters_done = it;
+      return s;
+    }
+    if (d < tol) {
+      ++it;
+      break;
+    }
+  }
+  if (iters_done) *iters_done = it;
+  if (last) *last = d;
+  return (d < tol) ? PQ_OK : PQ_ENOTCONV;
+}
+
+pq_status pq_get_Sigma(const pq_ctx *cc, double *out, size_t len) {
+  pq_ctx *c = const_cast<pq_ctx *>(cc);
+  if (!c || !out) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  size_t need = (size_t)2 * c->g.nk * c->g.n_ext;
+  if (len < need) return fail(c, PQ_EINVAL, "Sigma needs %zu doubles, got %zu", need, len);
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(out, c->b.sigma, need * sizeof(double), cudaMemcpyDeviceToHost));
+  return PQ_OK;
+}
+
+static pq_status get_matrix(pq_ctx *c, const void *base, int channel, int Q, double *out, size_t len) {
+  if (!out || channel < 0 || channel > 3 || Q < 0 || Q >= c->g.nQ)
+    return fail(c, PQ_EINVAL, "bad channel %d or Q %d", channel, Q);
+  const size_t nn = (size_t)c->g.n * c->g.n;
+  if (len < 2 * nn) return fail(c, PQ_EINVAL, "matrix needs %zu doubles, got %zu", 2 * nn, len);
+  CK(cudaStreamSynchronize(c->st));
+  const size_t off = ((size_t)channel * c->g.nQ + Q) * nn;
+  if (!c->c64) {
+    CK(cudaMemcpy(out, (const double2 *)base + off, nn * sizeof(double2), cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float2> tmp(nn);
+    CK(cudaMemcpy(tmp.data(), (const float2 *)base + off, nn * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < nn; ++i) {
+      out[2 * i] = tmp[i].x;
+      out[2 * i + 1] = tmp[i].y;
+    }
+  }
+  return PQ_OK;
+}
+
+pq_status pq_get_F(const pq_ctx *cc, int channel, int Q, double *out, size_t len) {
+  pq_ctx *c = const_cast<pq_ctx *>(cc);
+  if (!c) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (c->iterations == 0) return fail(c, PQ_EINVAL, "no iteration has run yet");
+  return get_matrix(c, c->b.fv, channel, Q, out, len);
+}
+
+pq_status pq_get_Phi(const pq_ctx *cc, int channel, int Q, double *out, size_t len) {
+  pq_ctx *c = const_cast<pq_ctx *>(cc);
+  if (!c) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  return get_matrix(c, c->b.phi, channel, Q, out, len);
+}
+
+pq_status pq_get_chi(const pq_ctx *cc, int channel, double *out, size_t len) {
+  pq_ctx *c = const_cast<pq_ctx *>(cc);
+  if (!c || !out) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (channel < 0 || channel > 3) return fail(c, PQ_EINVAL, "bad channel %d", channel);
+  if (c->iterations == 0) return fail(c, PQ_EINVAL, "no iteration has run yet");
+  if (len < (size_t)2 * c->g.nQ) return fail(c, PQ_EINVAL, "chi needs %d doubles", 2 * c->g.nQ);
+  CK(pq::launch_chi(c->st, c->g, c->b, c->c64));
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(out, c->b.chi + (size_t)channel * c->g.nQ, sizeof(double2) * c->g.nQ, cudaMemcpyDeviceToHost));
+  return PQ_OK;
+}
+
+pq_status pq_set_state(pq_ctx *c, const double *phi, const double *sigma) {
+  if (!c) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  CK(cudaStreamSynchronize(c->st));
+  if (sigma) CK(cudaMemcpy(c->b.sigma, sigma, sizeof(double2) * c->g.nk * c->g.n_ext, cudaMemcpyHostToDevice));
+  if (phi) {
+    const long long ne = 4LL * c->g.nQ * c->g.n * c->g.n;
+    if (!c->c64) {
+      CK(cudaMemcpy(c->b.phi, phi, ne * sizeof(double2), cudaMemcpyHostToDevice));
+    } else {
+      // stage through the F buffer, which the next iteration overwrites
+      const long long chunk = vbytes(c) / sizeof(double2);
+      for (long long o = 0; o < ne; o += chunk) {
+        long long cnt = std::min(chunk, ne - o);
+        CK(cudaMemcpy(c->b.fv, phi + 2 * o, cnt * sizeof(double2), cudaMemcpyHostToDevice));
+        phi_from_c128<<<(unsigned)((cnt + 255) / 256), 256>>>((float2 *)c->b.phi + o, (const double2 *)c->b.fv,
+                                                               cnt);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+      }
+    }
+  }
+  return PQ_OK;
+}
+
+pq_status pq_get_sizes(const pq_ctx *c, long long *o) {
+  if (!c || !o) return PQ_EINVAL;
+  o[0] = c->g.nk;
+  o[1] = c->g.n;
+  o[2] = c->g.nQ;
+  o[3] = c->g.n_ext;
+  o[4] = c->g.n_nu;
+  o[5] = c->g.n_om;
+  o[6] = (long long)c->bytes;
+  o[7] = c->c64 ? 8 : 16;
+  return PQ_OK;
+}
+
+pq_status pq_step_times(const pq_ctx *c, float *out, int n) {
+  if (!c || !out || n < PQ_NSTEPS) return PQ_EINVAL;
+  for (int i = 0; i < PQ_NSTEPS; ++i) out[i] = c->times[i];
+  return PQ_OK;
+}
+
+const char *pq_step_name(int i) { return (i >= 0 && i < PQ_NSTEPS) ? kStepNames[i] : ""; }
+
+const char *pq_last_error(const pq_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+void pq_destroy(pq_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  for (int i = 0; i <= PQ_NSTEPS; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  release_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Host-side launchers shared by the translation units of the solver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pq_common.cuh"
+
+namespace pq {
+
+// Device buffers of one solve.  Vertex arrays (phi, gam, fv) hold
+// 4 * nQ * n * n elements of the storage type (double2 or float2).
+struct Buffers {
+  void *phi = nullptr;   // reducible vertices Phi_r(Q)[k][k'], the state
+  void *gam = nullptr;   // BSE left operand s_r Gamma_r(Q) diag(X_r(Q))
+  void *fv = nullptr;    // full vertex F_r(Q)
+  double2 *sigma = nullptr;      // [nk][n_ext] state
+  double2 *sigma_new = nullptr;  // [nk][n_ext] Sigma of this iteration
+  double2 *sigma1 = nullptr;     // [nk][n_ext] Sigma~1
+  double2 *sigma2 = nullptr;     // [nk][n_ext] Sigma~2
+  double2 *gtab = nullptr;       // [nk][n_g] G on the table range
+  double2 *xph = nullptr;        // [nQ][n] (T/N) G(k) G(k+q)
+  double2 *xpp = nullptr;        // [nQ][n] (T/N) G(k) G(q-k)
+  double2 *k1 = nullptr;         // [4][nQ]
+  double2 *k2row = nullptr;      // [4][n][nQ]  (row leg k major, transfer fastest)
+  double2 *k2col = nullptr;      // [4][n][nQ]
+  double2 *dfpart = nullptr;     // [n][nk] dF part of Sigma, one partial per (k, k'-momentum)
+  double *scal = nullptr;        // [0] c1 of the Sigma tail, [1] max |dSigma| bits, [2] non-finite flag
+  // Sigma~1 in imaginary time
+  double2 *s1_R = nullptr;       // [nk][2M] Matsubara remainders
+  double2 *s1_E = nullptr;       // [2M][ntau] exp(-i nu_n tau_j)
+  double2 *s1_Ef = nullptr;      // [ntau][n_ext] w_j exp(i nu_n tau_j)
+  double2 *s1_ph = nullptr;      // [nk][nk] exp(i k.r) / N   (rows r)
+  double2 *s1_phc = nullptr;     // [nk][nk] exp(-i k.r)      (rows k)
+  double2 *s1_gkt = nullptr;     // [nk][ntau]
+  double2 *s1_grt = nullptr;     // [nk][ntau]
+  double2 *s1_srn = nullptr;     // [nk][n_ext]
+  double *s1_tau = nullptr;      // [ntau]
+  // Sigma~2 tables
+  double2 *s2_bph = nullptr;     // [nQ][nj] sum_j G(j) G(j+P)
+  double2 *s2_bpp = nullptr;     // [nQ][nj] sum_j G(P-j) G(j)
+  double2 *s2_cph = nullptr;     // [2][nQ][n_nu] C-weighted ph tables (d-m, m)
+  double2 *s2_cpp = nullptr;     // [nQ][n_nu] C-weighted pp table (s+t)
+  double2 *chi = nullptr;        // [4][nQ]
+};
+
+struct Sizes {
+  int ntau, M;  // tau nodes, Matsubara cut of G(tau)
+  int j_lo, nj; // frequency range of the Sigma~2 bubble tables
+};
+
+cudaError_t zgemm_fp64(cudaStream_t st, int M, int N, int K, double2 alpha, const double2 *A, int lda, long long sA,
+                       const double2 *B, int ldb, long long sB, double2 beta, double2 *C, int ldc, long long sC,
+                       int batch);
+
+// one-particle steps (pq_onebody.cu)
+cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b);
+cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b);
+cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);
+cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b);
+cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
+
+// vertex steps (pq_vertex.cu)
+cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
+cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64, const double *lam4);
+size_t assemble_smem_bytes(const Grid &g, bool c64);
+
+// Sigma~2 (pq_sigma2.cu)
+cudaError_t launch_sigma2(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);
+
+}  // namespace pq

@@ -1,0 +1,227 @@
+// One-particle steps of a parquet iteration: the Dyson equation
+// (App. A, Eq. PA_Dyson), the bubbles G G of the Bethe-Salpeter equations
+// (Eq. PA_F_Phi), the second-order self-energy Sigma~1 in imaginary time
+// (Sec. II.B), the assembly and mixing of Sigma, and the susceptibility.
+// All arithmetic here is FP64.
+#include <cstdio>
+
+#include "pq_common.cuh"
+#include "pq_internal.h"
+
+namespace pq {
+
+namespace {
+
+// c1 of Sigma ~ c1/(i nu) beyond the stored range: -nu Im Sigma at the two
+// outer stored frequencies, averaged over them and over momenta.
+__global__ void tail_c1_kernel(Grid g, const double2 *__restrict__ sigma, double *scal) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const double nlo = nu_of(g, g.e_lo), nhi = nu_of(g, g.e_hi);
+  for (int ik = threadIdx.x; ik < g.nk; ik += blockDim.x) {
+    s += -(nlo * sigma[(long long)ik * g.n_ext].y + nhi * sigma[(long long)ik * g.n_ext + g.n_ext - 1].y) * 0.5;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scal[0] = red[0] / g.nk;
+}
+
+__device__ inline double2 sigma_at(const Grid &g, const double2 *sigma, double c1, int ik, int n) {
+  if (n >= g.e_lo && n <= g.e_hi) return sigma[(long long)ik * g.n_ext + (n - g.e_lo)];
+  return make_double2(0.0, -c1 / nu_of(g, n));  // c1 / (i nu)
+}
+
+// Dyson equation G = [G0^-1 - Sigma]^-1 on the table range.
+__global__ void green_kernel(Grid g, const double2 *__restrict__ sigma, const double *__restrict__ scal,
+                             double2 *__restrict__ gtab) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nk * g.n_g) return;
+  int ik = i / g.n_g, n = g.g_lo + i % g.n_g;
+  double2 s = sigma_at(g, sigma, scal[0], ik, n);
+  gtab[i] = cinv(g0_inverse(g, ik, n) - s);
+}
+
+__device__ inline double2 gt(const Grid &g, const double2 *gtab, int ik, int n) {
+  return gtab[(long long)ik * g.n_g + (n - g.g_lo)];
+}
+
+// X_ph(Q,k) = (T/N) G(k) G(k+q), X_pp(Q,k) = (T/N) G(k) G(q-k).
+__global__ void bubbles_kernel(Grid g, const double2 *__restrict__ gtab, double2 *__restrict__ xph,
+                               double2 *__restrict__ xpp) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)g.nQ * g.n) return;
+  int Q = (int)(i / g.n), k = (int)(i % g.n);
+  int iq = Q / g.n_om, m = g.m_lo + Q % g.n_om;
+  int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
+  double c = g.T / g.nk;
+  double2 gk = gt(g, gtab, ik, n);
+  xph[i] = c * cmul(gk, gt(g, gtab, kadd(g, ik, iq), n + m));
+  xpp[i] = c * cmul(gk, gt(g, gtab, ksub(g, iq, ik), m - n - 1));
+}
+
+// Tail moments of G = 1/(i nu) + c2/(i nu)^2 + c3/(i nu)^3 + O(nu^-4).
+__device__ inline void tail_moments(const Grid &g, double c1, int ik, double &c2, double &c3) {
+  if (g.lattice == 1) {
+    int ix = ik / g.L, iy = ik % g.L;
+    double a = -2.0 * g.hop * (cospi(2.0 * ix / g.L) + cospi(2.0 * iy / g.L)) - g.mu;
+    c2 = a;
+    c3 = a * a + c1;
+  } else {
+    c2 = 0.0;
+    c3 = 0.25 * g.hop * g.hop + c1;
+  }
+}
+
+// Matsubara remainders R(k, n) = G(k, n) - tails, n in [-M, M-1].
+__global__ void s1_remainder_kernel(Grid g, int M, const double2 *__restrict__ sigma, const double *__restrict__ scal,
+                                    double2 *__restrict__ R) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nk * 2 * M) return;
+  int ik = i / (2 * M), n = -M + i % (2 * M);
+  double c1 = scal[0], c2, c3;
+  tail_moments(g, c1, ik, c2, c3);
+  double2 G = cinv(g0_inverse(g, ik, n) - sigma_at(g, sigma, c1, ik, n));
+  double nu = nu_of(g, n);
+  // 1/(i nu) = -i/nu; 1/(i nu)^2 = -1/nu^2; 1/(i nu)^3 = i/nu^3
+  double2 tail = make_double2(-c2 / (nu * nu), -1.0 / nu + c3 / (nu * nu * nu));
+  R[i] = G - tail;
+}
+
+// G(k, tau) += analytic transforms of the subtracted tails (0 < tau < beta):
+// 1/(i nu) -> -1/2, 1/(i nu)^2 -> tau/2 - beta/4, 1/(i nu)^3 -> tau (beta - tau)/4.
+__global__ void s1_tails_kernel(Grid g, int ntau, const double *__restrict__ tau, const double *__restrict__ scal,
+                                double2 *__restrict__ gkt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nk * ntau) return;
+  int ik = i / ntau, j = i % ntau;
+  double c2, c3;
+  tail_moments(g, scal[0], ik, c2, c3);
+  double t = tau[j], b = g.beta;
+  gkt[i].x += -0.5 + c2 * (0.5 * t - 0.25 * b) + c3 * t * (b - t) * 0.25;
+}
+
+// Sigma(r, tau) = -U^2 G(r,tau)^2 G(-r,-tau) = U^2 G(r,tau)^2 G(-r, beta - tau);
+// the nodes are symmetric about beta/2, so beta - tau_j is node ntau-1-j.
+__global__ void s1_product_kernel(Grid g, int ntau, const double2 *__restrict__ grt, double2 *__restrict__ srt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nk * ntau) return;
+  int ir = i / ntau, j = i % ntau;
+  double2 a = grt[i];
+  double2 b = grt[(long long)kneg(g, ir) * ntau + (ntau - 1 - j)];
+  srt[i] = (g.U * g.U) * cmul(cmul(a, a), b);
+}
+
+// Sigma_new = Sigma~1 + Sigma~2 + dF part; max |Sigma_new - Sigma|; Sigma <- mix.
+__global__ void sigma_update_kernel(Grid g, const double2 *__restrict__ s1, const double2 *__restrict__ s2,
+                                    const double2 *__restrict__ dfpart, double2 *__restrict__ sigma,
+                                    double2 *__restrict__ sigma_new, double *scal) {
+  __shared__ double red[256];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  bool bad = false;
+  if (i < g.nk * g.n_ext) {
+    int ik = i / g.n_ext, n = g.e_lo + i % g.n_ext;
+    double2 s = s1[i] + s2[i];
+    if (n >= g.n_lo && n <= g.n_hi) {
+      int k = ik * g.n_nu + (n - g.n_lo);
+      for (int j = 0; j < g.nk; ++j) s = s + dfpart[(long long)k * g.nk + j];
+    }
+    double2 old = sigma[i];
+    sigma_new[i] = s;
+    d = sqrt(cabs2(s - old));
+    bad = !(isfinite(s.x) && isfinite(s.y));
+    sigma[i] = g.mix * s + (1.0 - g.mix) * old;
+  }
+  red[threadIdx.x] = bad ? 1e300 : d;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMax((unsigned long long *)&scal[1], (unsigned long long)__double_as_longlong(red[0]));
+    if (red[0] >= 1e300) scal[2] = 1.0;
+  }
+}
+
+// chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k'); one block per (r, Q).
+template <typename S>
+__global__ void chi_kernel(Grid g, const S *__restrict__ fv, const double2 *__restrict__ xph,
+                           const double2 *__restrict__ xpp, double2 *__restrict__ chi) {
+  __shared__ double2 red[256];
+  int r = blockIdx.y, Q = blockIdx.x;
+  const double2 *X = (r < 2 ? xph : xpp) + (long long)Q * g.n;
+  const S *F = fv + ((long long)r * g.nQ + Q) * g.n * g.n;
+  double2 acc = make_double2(0.0, 0.0);
+  int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  for (int k = warp; k < g.n; k += nw) {
+    double2 rs = make_double2(0.0, 0.0);
+    for (int kp = lane; kp < g.n; kp += 32) rs = cfma(to_c<S, double2>(F[(long long)k * g.n + kp]), X[kp], rs);
+    acc = cfma(X[k], rs, acc);
+    if (lane == 0) acc = acc + X[k];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) chi[(long long)r * g.nQ + Q] = make_double2(-red[0].x, -red[0].y);
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b) {
+  tail_c1_kernel<<<1, 256, 0, st>>>(g, b.sigma, b.scal);
+  green_kernel<<<nblk((long long)g.nk * g.n_g, 256), 256, 0, st>>>(g, b.sigma, b.scal, b.gtab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b) {
+  bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b) {
+  const int M = z.M, nt = z.ntau;
+  s1_remainder_kernel<<<nblk((long long)g.nk * 2 * M, 256), 256, 0, st>>>(g, M, b.sigma, b.scal, b.s1_R);
+  cudaError_t e = zgemm_fp64(st, g.nk, nt, 2 * M, make_double2(g.T, 0.0), b.s1_R, 2 * M, 0, b.s1_E, nt, 0,
+                             make_double2(0.0, 0.0), b.s1_gkt, nt, 0, 1);
+  if (e != cudaSuccess) return e;
+  s1_tails_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, b.s1_tau, b.scal, b.s1_gkt);
+  e = zgemm_fp64(st, g.nk, nt, g.nk, make_double2(1.0, 0.0), b.s1_ph, g.nk, 0, b.s1_gkt, nt, 0,
+                 make_double2(0.0, 0.0), b.s1_grt, nt, 0, 1);
+  if (e != cudaSuccess) return e;
+  s1_product_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, b.s1_grt, b.s1_gkt);
+  e = zgemm_fp64(st, g.nk, g.n_ext, nt, make_double2(1.0, 0.0), b.s1_gkt, nt, 0, b.s1_Ef, g.n_ext, 0,
+                 make_double2(0.0, 0.0), b.s1_srn, g.n_ext, 0, 1);
+  if (e != cudaSuccess) return e;
+  e = zgemm_fp64(st, g.nk, g.n_ext, g.nk, make_double2(1.0, 0.0), b.s1_phc, g.nk, 0, b.s1_srn, g.n_ext, 0,
+                 make_double2(0.0, 0.0), b.sigma1, g.n_ext, 0, 1);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b) {
+  cudaMemsetAsync(b.scal + 1, 0, 2 * sizeof(double), st);
+  sigma_update_kernel<<<nblk((long long)g.nk * g.n_ext, 256), 256, 0, st>>>(g, b.sigma1, b.sigma2, b.dfpart,
+                                                                            b.sigma, b.sigma_new, b.scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64) {
+  dim3 grid(g.nQ, 4);
+  if (c64)
+    chi_kernel<float2><<<grid, 256, 0, st>>>(g, (const float2 *)b.fv, b.xph, b.xpp, b.chi);
+  else
+    chi_kernel<double2><<<grid, 256, 0, st>>>(g, (const double2 *)b.fv, b.xph, b.xpp, b.chi);
+  return cudaGetLastError();
+}
+
+}  // namespace pq

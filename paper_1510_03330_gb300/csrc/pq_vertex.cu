@@ -1,0 +1,275 @@
+// Vertex steps of a parquet iteration:
+//  * kernel functions K1, K2 of the reducible vertex (Sec. II.A: first level at
+//    the four corners of the frequency box, second level at the two frequency
+//    edges of the other leg, momentum averaged);
+//  * the parquet equations Gamma_r = Lambda_r + sum_i c_i Phi[crossed args]
+//    with the kernel fill (Eq. PA_F; App. A, Eqs. PA_Gamma_dm, PA_Gamma_st),
+//    F_r = Gamma_r + Phi_r (Eq. PA_F_G), the BSE left operand
+//    s_r Gamma_r diag(X_r) (Eq. PA_F_Phi), and the box sum of Eq. PA_Sigma over
+//    F - Lambda^0 used by the regulated self-energy (Sec. II.B).
+//
+// The crossed arguments are gathers across transfer slices.  For a fixed row
+// leg k every crossed map is an affine permutation of the (Q, k') plane of row
+// k, so one CTA per (k, k'-momentum) walks the q-momenta and, per step, loads
+// six frequency blocks [m~][n_c] (NOmega x Nnu each, coalesced along n_c):
+//   R_x = Phi_x[(k'-k, .)][k][(k+q, .)]   x = d, m   (maps A and C)
+//   P_x = Phi_x[(q, .)][k][(k', .)]        x = d, m   (own d/m, map D)
+//   S_x = Psi_x[(q', .)][k][(k', .)]       x = s, t   (map B, own s/t)
+// with q' = k + k' + q, and writes the d/m outputs at transfer q and the s/t
+// outputs at transfer q'.  Every element of Phi is read exactly once.
+#include "pq_common.cuh"
+#include "pq_internal.h"
+
+namespace pq {
+
+namespace {
+
+template <typename S>
+__device__ inline double2 ld2(const S *p) {
+  return to_c<S, double2>(*p);
+}
+
+// K1[r][Q], K2row[r][k][Q], K2col[r][k'][Q]; one block per (Q, r), FP64 sums.
+template <typename S>
+__global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__restrict__ k1,
+                               double2 *__restrict__ k2row, double2 *__restrict__ k2col) {
+  __shared__ double2 red[256];
+  __shared__ double2 sk1;
+  const int Q = blockIdx.x, r = blockIdx.y;
+  const long long n = g.n;
+  const S *V = phi + ((long long)r * g.nQ + Q) * n * n;
+  const int nn = g.n_nu, nk = g.nk;
+  // first level: four corners, all momentum pairs
+  double2 acc = make_double2(0.0, 0.0);
+  const int ncorner = 4 * nk * nk;
+  for (int c = threadIdx.x; c < ncorner; c += blockDim.x) {
+    int e = c & 3, pair = c >> 2;
+    int a = pair / nk, b = pair % nk;
+    int ra = a * nn + ((e & 1) ? nn - 1 : 0), cb = b * nn + ((e & 2) ? nn - 1 : 0);
+    acc = acc + ld2(V + ra * n + cb);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sk1 = (1.0 / ncorner) * red[0];
+    k1[(long long)r * g.nQ + Q] = sk1;
+  }
+  __syncthreads();
+  const double2 K1 = sk1;
+  const double inv = 1.0 / (2.0 * nk);
+  for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
+    double2 rs = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
+    for (int b = 0; b < nk; ++b) {
+      rs = rs + ld2(V + k * n + b * nn) + ld2(V + k * n + b * nn + nn - 1);
+      cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+    }
+    k2row[((long long)r * g.n + k) * g.nQ + Q] = inv * rs - K1;
+    k2col[((long long)r * g.n + k) * g.nQ + Q] = inv * cs - K1;
+  }
+}
+
+struct Lam {
+  double2 l[4];  // Lambda_r (parquet approximation: U, -U, 2U, 0)
+};
+
+template <typename C> __device__ inline C cz();
+template <> __device__ inline double2 cz<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ inline float2 cz<float2>() { return make_float2(0.f, 0.f); }
+template <typename C> __device__ inline C cfrom(double2 v);
+template <> __device__ inline double2 cfrom<double2>(double2 v) { return v; }
+template <> __device__ inline float2 cfrom<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <typename C, typename S> __device__ inline S cstore(C v);
+template <> __device__ inline double2 cstore<double2, double2>(double2 v) { return v; }
+template <> __device__ inline float2 cstore<float2, float2>(float2 v) { return v; }
+template <typename C> __device__ inline double2 cdbl(C v);
+template <> __device__ inline double2 cdbl<double2>(double2 v) { return v; }
+template <> __device__ inline double2 cdbl<float2>(float2 v) { return make_double2(v.x, v.y); }
+
+// S: storage type of vertices, C: arithmetic type (double2 for FP64, float2 for the split path).
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restrict__ phi, S *__restrict__ gam,
+                                                       S *__restrict__ fv, const double2 *__restrict__ k1,
+                                                       const double2 *__restrict__ k2row,
+                                                       const double2 *__restrict__ xph,
+                                                       const double2 *__restrict__ xpp,
+                                                       const double2 *__restrict__ gtab, double2 *__restrict__ dfpart,
+                                                       Lam lam) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NB = g.n_om * g.n_nu;
+  S *Rd = (S *)smem_raw;
+  S *Rm = Rd + NB;
+  S *Pd = Rm + NB;
+  S *Pm = Pd + NB;
+  S *Ss = Pm + NB;
+  S *St = Ss + NB;
+  C *FKd = (C *)(St + NB);  // K1 + K2row(k) at transfer (k'-k, m~), x = d
+  C *FKm = FKd + g.n_om;
+  __shared__ double2 red[256];
+
+  const int ikp = blockIdx.x, k = blockIdx.y;
+  const int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
+  const long long nn = g.n;
+  const long long slab = nn * nn;  // one (r, Q) matrix
+  const long long chan = (long long)g.nQ * slab;
+  const int tmom = ksub(g, ikp, ik);
+  const double2 *xph_ = xph, *xpp_ = xpp;
+
+  for (int t = threadIdx.x; t < 2 * g.n_om; t += blockDim.x) {
+    int x = t / g.n_om, mt = t % g.n_om;
+    int Qt = tmom * g.n_om + mt;
+    double2 v = k1[(long long)x * g.nQ + Qt] + k2row[((long long)x * g.n + k) * g.nQ + Qt];
+    (x == 0 ? FKd : FKm)[mt] = cfrom<C>(v);
+  }
+
+  const C l0 = cfrom<C>(lam.l[0]), l1 = cfrom<C>(lam.l[1]), l2 = cfrom<C>(lam.l[2]), l3 = cfrom<C>(lam.l[3]);
+  const double2 U2 = make_double2(2.0 * g.U, 0.0);
+  const C twoU = cfrom<C>(U2);
+  C acc = cz<C>();
+
+  for (int iq = 0; iq < g.nk; ++iq) {
+    const int iqp = kadd(g, kadd(g, ik, ikp), iq);
+    const int cmom = kadd(g, ik, iq);
+    const int pqk = ksub(g, iqp, ik);  // momentum of q' - k
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB; e += blockDim.x) {
+      const int mt = e / g.n_nu, c = e % g.n_nu;
+      const long long rrow = ((long long)(tmom * g.n_om + mt) * nn + k) * nn + cmom * g.n_nu + c;
+      const long long prow = ((long long)(iq * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
+      const long long srow = ((long long)(iqp * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
+      Rd[e] = phi[rrow];
+      Rm[e] = phi[chan + rrow];
+      Pd[e] = phi[prow];
+      Pm[e] = phi[chan + prow];
+      Ss[e] = phi[2 * chan + srow];
+      St[e] = phi[3 * chan + srow];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB; e += blockDim.x) {
+      const int mi = e / g.n_nu, npi = e % g.n_nu;
+      const int m = g.m_lo + mi, np_ = g.n_lo + npi;
+      // ---------------- d/m at Q = (q, m)
+      const int mt = np_ - n;  // transfer k' - k of maps A and C
+      const bool inT = (mt >= g.m_lo && mt <= g.m_hi);
+      const int ti = mt - g.m_lo;
+      C Ad = cz<C>(), Am = cz<C>();
+      const int nc = n + m;  // column k + q of map A
+      if (inT) {
+        if (nc >= g.n_lo && nc <= g.n_hi) {
+          Ad = to_c<S, C>(Rd[ti * g.n_nu + nc - g.n_lo]);
+          Am = to_c<S, C>(Rm[ti * g.n_nu + nc - g.n_lo]);
+        } else {
+          Ad = FKd[ti];
+          Am = FKm[ti];
+        }
+      }
+      C Bs = cz<C>(), Bt = cz<C>();
+      const int mb = n + np_ + m + 1;  // transfer k + k' + q of map B
+      if (mb >= g.m_lo && mb <= g.m_hi) {
+        Bs = to_c<S, C>(Ss[(mb - g.m_lo) * g.n_nu + npi]);
+        Bt = to_c<S, C>(St[(mb - g.m_lo) * g.n_nu + npi]);
+      }
+      const C od = to_c<S, C>(Pd[e]), om = to_c<S, C>(Pm[e]);
+      const C Gd = l0 + (-0.5f) * Ad + (-1.5f) * Am + 0.5f * Bs + 1.5f * Bt;
+      const C Gm = l1 + (-0.5f) * Ad + 0.5f * Am + (-0.5f) * Bs + 0.5f * Bt;
+      const C Fd = Gd + od, Fm = Gm + om;
+      const int Q = iq * g.n_om + mi;
+      const long long o_dm = ((long long)Q * nn + k) * nn + ikp * g.n_nu + npi;
+      const C xq = cfrom<C>(xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
+      gam[o_dm] = cstore<C, S>(cmul(Gd, xq));
+      gam[chan + o_dm] = cstore<C, S>(cmul(Gm, xq));
+      fv[o_dm] = cstore<C, S>(Fd);
+      fv[chan + o_dm] = cstore<C, S>(Fm);
+      // Eq. PA_Sigma, ph part: G(k+q) X_ph(Q,k') [F_d - F_m - (Lambda0_d - Lambda0_m)]
+      const C gkq = cfrom<C>(gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
+      acc = cfma(cmul(gkq, xq), Fd - Fm - twoU, acc);
+
+      // ---------------- s/t at Q' = (q', m)
+      C Cd = cz<C>(), Cm = cz<C>();
+      const int nc2 = m - np_ - 1;  // column q' - k' of map C
+      if (inT) {
+        if (nc2 >= g.n_lo && nc2 <= g.n_hi) {
+          Cd = to_c<S, C>(Rd[ti * g.n_nu + nc2 - g.n_lo]);
+          Cm = to_c<S, C>(Rm[ti * g.n_nu + nc2 - g.n_lo]);
+        } else {
+          Cd = FKd[ti];
+          Cm = FKm[ti];
+        }
+      }
+      C Dd = cz<C>(), Dm = cz<C>();
+      const int md = m - n - np_ - 1;  // transfer q' - k - k' = q of map D
+      if (md >= g.m_lo && md <= g.m_hi) {
+        Dd = to_c<S, C>(Pd[(md - g.m_lo) * g.n_nu + npi]);
+        Dm = to_c<S, C>(Pm[(md - g.m_lo) * g.n_nu + npi]);
+      }
+      const C os = to_c<S, C>(Ss[e]), ot = to_c<S, C>(St[e]);
+      const C Gs = l2 + 0.5f * Cd + (-1.5f) * Cm + 0.5f * Dd + (-1.5f) * Dm;
+      const C Gt = l3 + (-0.5f) * Cd + (-0.5f) * Cm + 0.5f * Dd + 0.5f * Dm;
+      const C Fs = Gs + os, Ft = Gt + ot;
+      const int Qp = iqp * g.n_om + mi;
+      const long long o_st = ((long long)Qp * nn + k) * nn + ikp * g.n_nu + npi;
+      const C xqp = cfrom<C>(xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
+      gam[2 * chan + o_st] = cstore<C, S>((-0.5f) * cmul(Gs, xqp));
+      gam[3 * chan + o_st] = cstore<C, S>(0.5f * cmul(Gt, xqp));
+      fv[2 * chan + o_st] = cstore<C, S>(Fs);
+      fv[3 * chan + o_st] = cstore<C, S>(Ft);
+      // pp part: G(q'-k) X_pp(Q',k') [F_s + F_t - (Lambda0_s + Lambda0_t)]
+      const C gqk = cfrom<C>(gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
+      acc = cfma(cmul(gqk, xqp), Fs + Ft - twoU, acc);
+    }
+  }
+  red[threadIdx.x] = cdbl<C>(acc);
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // -(U/4)(T/N)^2 sum GGG: one T/N sits in X
+    double pref = -(g.U * 0.25) * g.T / g.nk;
+    dfpart[(long long)k * g.nk + ikp] = pref * red[0];
+  }
+}
+
+}  // namespace
+
+size_t assemble_smem_bytes(const Grid &g, bool c64) {
+  size_t es = c64 ? sizeof(float2) : sizeof(double2);
+  return 6 * (size_t)g.n_om * g.n_nu * es + 2 * (size_t)g.n_om * es;
+}
+
+cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64) {
+  dim3 grid(g.nQ, 4);
+  if (c64)
+    kernels_kernel<float2><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col);
+  else
+    kernels_kernel<double2><<<grid, 256, 0, st>>>(g, (const double2 *)b.phi, b.k1, b.k2row, b.k2col);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64, const double *lam4) {
+  Lam lam;
+  for (int r = 0; r < 4; ++r) lam.l[r] = make_double2(lam4[2 * r], lam4[2 * r + 1]);
+  dim3 grid(g.nk, g.n);
+  size_t sm = assemble_smem_bytes(g, c64);
+  cudaError_t e;
+  if (c64) {
+    auto kfn = assemble_kernel<float2, float2>;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kfn<<<grid, 256, sm, st>>>(g, (const float2 *)b.phi, (float2 *)b.gam, (float2 *)b.fv, b.k1, b.k2row, b.xph,
+                               b.xpp, b.gtab, b.dfpart, lam);
+  } else {
+    auto kfn = assemble_kernel<double2, double2>;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kfn<<<grid, 256, sm, st>>>(g, (const double2 *)b.phi, (double2 *)b.gam, (double2 *)b.fv, b.k1, b.k2row, b.xph,
+                               b.xpp, b.gtab, b.dfpart, lam);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pq
