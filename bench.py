@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of one self-consistent parquet iteration on GB300.
+
+A step is one parquet iteration (Dyson, bubbles, kernel functions, parquet
+equations with the kernel fill, regulated Schwinger-Dyson self-energy,
+Bethe-Salpeter products, mixing) of a seeded synthetic Hubbard workload.
+`value` is whole-job iterations per second with the state resident in HBM;
+`e2e` is the same metric through the public API from a fresh context,
+including its set-up, with the self-energy copied to host every step.
+
+  python bench.py [--gpus N --steps K --warmup W --workload NAME --precision P]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+With N > 1 (torchrun, one process per GPU) every rank runs its own replica
+solve: the solves are independent, so no collective touches the data path
+(weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1510_03330_gb300.workloads import CONFIGS, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_TF32X3  # noqa: E402
+
+METRIC = "parquet iter/s and BSE TFLOP/s: split-precision vs FP64 path at a stated Σ error"
+UNIT = "iter/s"
+DEFAULT_WORKLOAD = "square4_u2_b5"
+DEFAULT_PRECISION = FP64
+# kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
+# Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
+LAUNCHES_PER_ITER = 18
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, nominal
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def describe(name, p, precision):
+    return {
+        "workload": f"{name}: {p.lattice} lattice {p.L}x{p.L} k, Nnu={p.n_nu}, NOmega={p.n_Omega}, U={p.U}, "
+                    f"beta={p.beta}, mu={p.mu}; BSE {4 * p.n_Q} complex GEMMs of {p.n}^3",
+        "precision": precision,
+        "n": p.n,
+        "N_Q": p.n_Q,
+        "l2": "inputs larger than L2 (vertex arrays of several GB are streamed every step)",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(p, target_s=20.0):
+    """Time the FP64 oracle on a bounded sample of one iteration from the zero
+    state and extrapolate to the full iteration.  Every step runs in full
+    except the per-slice ones: assembly + BSE on a sample of transfer slices,
+    Sigma~2 on a sample of outputs, the dF box sum on a sample of row legs."""
+    from oracle import parquet_oracle as O
+
+    g = O.make_grid(p)
+    rng = np.random.default_rng(1510)
+    phi = np.broadcast_to(np.zeros((), np.complex128), (4, p.n_Q, p.n, p.n))  # the zero state, held as a view
+    sigma = np.zeros((p.n_k, p.n_ext), np.complex128)
+    lam = O.lambda0(p.U)
+    t = {}
+    t0 = time.perf_counter()
+    G = O.Propagator(g, sigma)
+    X = O.bubbles(g, G)
+    K = O.extract_kernels(g, phi)
+    s1 = O.sigma1_second_order(g, sigma)
+    t["full_steps"] = time.perf_counter() - t0
+    del s1
+    # per-slice steps: add samples round-robin until about target_s seconds of work
+    cost = {"slice": [0, 0.0], "out": [0, 0.0], "row": [0, 0.0]}
+    start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        Qs = rng.choice(p.n_Q, 1, replace=False)
+        gam, F = O.assemble(g, phi, K, lam, Qs=Qs)
+        for r in range(4):
+            Xr = (X[0] if r < 2 else X[1])[Qs]
+            O.BSE_SIGN[r] * np.matmul(gam[r] * Xr[:, None, :], F[r])
+        cost["slice"][0] += 1
+        cost["slice"][1] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.sigma2_kernel_terms(g, G, K, outputs=[(int(rng.integers(g.nk)), int(rng.integers(g.e_lo, g.e_hi + 1)))])
+        cost["out"][0] += 1
+        cost["out"][1] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ks = rng.choice(p.n, 1, replace=False)
+        gam_r, F_r = O.assemble(g, phi, K, lam, ks=ks)
+        O.sigma_delta_F(g, G, F_r, K, lam, ks=ks)
+        cost["row"][0] += 1
+        cost["row"][1] += time.perf_counter() - t0
+        if time.perf_counter() - start + t["full_steps"] > target_s:
+            break
+    per = {k: v[1] / v[0] for k, v in cost.items()}
+    total = t["full_steps"] + per["slice"] * p.n_Q + per["out"] * g.nk * p.n_ext + per["row"] * p.n
+    sampled = t["full_steps"] + sum(v[1] for v in cost.values())
+    sample = (f"one iteration from the zero state: Dyson, bubbles, K1/K2, Sigma~1 in full; assembly+BSE on "
+              f"{cost['slice'][0]}/{p.n_Q} transfer slices, Sigma~2 on {cost['out'][0]}/{g.nk * p.n_ext} "
+              f"outputs, dF sum on {cost['row'][0]}/{p.n} row legs; {sampled:.1f} s measured, extrapolated "
+              f"linearly to {total:.1f} s per iteration")
+    return 1.0 / total, sample, sampled
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return max(i.get("num_threads", 1) for i in threadpool_info())
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- main
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(CONFIGS))
+    ap.add_argument("--precision", default=DEFAULT_PRECISION,
+                    choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_BF16X6])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    p = CONFIGS[a.workload]
+    cfg = describe(a.workload, p, a.precision)
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+
+    if a.impl == "reference":
+        if rank != 0:
+            return 0
+        v, sample, secs = oracle_sample(p)
+        cores = blas_threads()
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1510_03330_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_1510_03330_gb300.binding import Solver
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    solver = Solver(p, precision=a.precision, time_steps=True)
+    for _ in range(a.warmup):
+        solver.iterate(1)
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_sum = {}
+    e0.record(stream)
+    for _ in range(a.steps):
+        solver.iterate(1)
+        for k, v in solver.step_times().items():
+            step_sum[k] = step_sum.get(k, 0.0) + v
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * a.steps / (ms / 1e3)
+    dev_bytes = solver.device_bytes
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+
+    # roofline of the dominant kernel, timed live by the library's events on its stream
+    pk, src = peaks()
+    esz = 16 if a.precision == FP64 else 8
+    n, nQ = p.n, p.n_Q
+    steps = {k: v / a.steps for k, v in step_sum.items() if k != "total"}
+    top = max(steps, key=steps.get)
+    bse_flops = 8.0 * n**3 * 4 * nQ
+    remap_bytes = 12.0 * nQ * n * n * esz
+    bse_tflops = bse_flops / (steps["bse"] * 1e-3) / 1e12
+    remap_gbs = remap_bytes / (steps["assemble"] * 1e-3) / 1e9
+    if a.precision == FP64:
+        bse_roof = {"bound": "alu", "achieved": bse_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                    "frac": bse_tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+    else:
+        ratio = {SPLIT_TF32X3: 1.1 / 2.25, SPLIT_BF16X3: 1.0, SPLIT_BF16X6: 1.0}[a.precision]
+        peak = pk["bf16_tflops"] * ratio
+        bse_roof = {"bound": "tensor", "achieved": bse_tflops, "peak": peak, "unit": "TFLOP/s",
+                    "frac": bse_tflops / peak, "traffic": None,
+                    "peak_source": f"{src} bf16 burst x nominal ratio {ratio:.3f}"}
+    remap_roof = {"bound": "hbm", "achieved": remap_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                  "frac": remap_gbs / pk["hbm_gbs"], "traffic": None, "peak_source": f"{src} copy bandwidth"}
+    roof = bse_roof if top == "bse" else (remap_roof if top == "assemble" else bse_roof)
+    roof = dict(roof, kernel=top)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if a.precision == FP64 else "f32 (split operands, fp32 accumulate)",
+            "data": "synthetic", "config": cfg, "roofline": roof,
+            "kernels": {"ms_per_iter": steps, "bse": bse_roof, "assemble": remap_roof},
+            "bse_tflops": bse_tflops, "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
+            "device_bytes": dev_bytes}
+
+    if not a.no_e2e:
+        # end to end through the public API: a fresh context (set-up, table uploads), K iterations
+        # each followed by a device->host copy of Sigma, then chi read back
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        s = Solver(p, precision=a.precision)
+        for _ in range(a.steps):
+            s.iterate(1)
+            sig = s.sigma()
+        chi = s.chi(1)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s.close()
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        M, ntau = p.tau_matsubara, p.tau_panels * p.tau_order
+        h2d = 16 * (2 * M * ntau + ntau * p.n_ext + 2 * p.n_k**2) + 8 * ntau
+        line["e2e"] = {"value": world * a.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
+                       "d2h_bytes_per_step": sig.nbytes + chi.nbytes / a.steps,
+                       "note": "includes context set-up and the upload of the imaginary-time transform tables"}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, sample, secs = oracle_sample(p)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

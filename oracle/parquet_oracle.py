@@ -228,10 +228,9 @@ def extract_kernels(g: Grid, phi):
     nk, nn = g.nk, p.n_nu
     v = phi.reshape(4, p.n_Q, nk, nn, nk, nn)
     edges = [0, nn - 1]
-    corner = np.stack([v[:, :, :, a, :, b] for a in edges for b in edges], 0)  # (4c, 4r, Q, k, k')
-    K1 = corner.mean(axis=(0, 3, 4))
-    rows = np.stack([v[:, :, :, :, :, b] for b in edges], 0).mean(axis=(0, 5))  # (4, Q, k, n)
-    cols = np.stack([v[:, :, :, a, :, :] for a in edges], 0).mean(axis=(0, 3))  # (4, Q, k', n')
+    K1 = sum(v[:, :, :, a, :, b].mean(axis=(2, 3)) for a in edges for b in edges) / 4.0
+    rows = sum(v[:, :, :, :, :, b].mean(axis=4) for b in edges) / 2.0  # (4, Q, k, n)
+    cols = sum(v[:, :, :, a, :, :].mean(axis=2) for a in edges) / 2.0  # (4, Q, k', n')
     K2row = rows.reshape(4, p.n_Q, p.n) - K1[:, :, None]
     K2col = cols.reshape(4, p.n_Q, p.n) - K1[:, :, None]
     return K1, K2row, K2col
@@ -304,17 +303,20 @@ def parquet_gamma(g: Grid, r, lam_r, lookup, k, n, kp, np_, q, m):
     return out
 
 
-def assemble(g: Grid, phi, K, lam):
-    """Gamma_r and F_r = Gamma_r + Phi_r on the whole box (Eqs. PA_F, PA_F_G)."""
+def assemble(g: Grid, phi, K, lam, Qs=None, ks=None):
+    """Gamma_r and F_r = Gamma_r + Phi_r (Eqs. PA_F, PA_F_G) on the box, or on the
+    transfer slices Qs and row legs ks only (all columns k')."""
     p = g.p
     kk, kn, qk, qm = box_indices(g)
-    q3, k3, kp3 = qk[:, None, None], kk[None, :, None], kk[None, None, :]
-    m3, n3, np3 = qm[:, None, None], kn[None, :, None], kn[None, None, :]
+    Qs = np.arange(p.n_Q) if Qs is None else np.asarray(Qs)
+    ks = np.arange(p.n) if ks is None else np.asarray(ks)
+    q3, k3, kp3 = qk[Qs][:, None, None], kk[ks][None, :, None], kk[None, None, :]
+    m3, n3, np3 = qm[Qs][:, None, None], kn[ks][None, :, None], kn[None, None, :]
     lookup = lambda x, a, b, tr: vertex_value(g, phi, K, x, a, b, tr)  # noqa: E731
-    gamma = np.empty((4, p.n_Q, p.n, p.n), dtype=np.complex128)
+    gamma = np.empty((4, Qs.size, ks.size, p.n), dtype=np.complex128)
     for r in range(4):
         gamma[r] = parquet_gamma(g, r, lam[r], lookup, k3, n3, kp3, np3, q3, m3)
-    return gamma, gamma + phi
+    return gamma, gamma + phi[:, Qs][:, :, ks]
 
 
 def aux_vertex_minus_lambda0(g: Grid, K, r, k, n, kp, np_, q, m):
@@ -348,20 +350,22 @@ def sde_weights(g: Grid, G: Propagator, k, n, kp, np_, q, m):
     return ph, pp
 
 
-def sigma_delta_F(g: Grid, G: Propagator, F, K, lam):
+def sigma_delta_F(g: Grid, G: Propagator, F, K, lam, ks=None):
     """Box part of the regulated self-energy (Sec. II.B):
-    -(U/4)(T/N)^2 sum_{k',q in box} [GGG (dF_d - dF_m) + GGG (dF_s + dF_t)], dF = F - F~."""
+    -(U/4)(T/N)^2 sum_{k',q in box} [GGG (dF_d - dF_m) + GGG (dF_s + dF_t)], dF = F - F~,
+    for every k of the box, or for the row legs ks given F[:, :, ks, :]."""
     p = g.p
     kk, kn, qk, qm = box_indices(g)
-    q3, k3, kp3 = qk[:, None, None], kk[None, :, None], kk[None, None, :]
-    m3, n3, np3 = qm[:, None, None], kn[None, :, None], kn[None, None, :]
+    ks = np.arange(p.n) if ks is None else np.asarray(ks)
+    q3, k3, kp3 = qk[:, None, None], kk[ks][None, :, None], kk[None, None, :]
+    m3, n3, np3 = qm[:, None, None], kn[ks][None, :, None], kn[None, None, :]
     l0 = lambda0(p.U)
     dF = [F[r] - l0[r] - aux_vertex_minus_lambda0(g, K, r, k3, n3, kp3, np3, q3, m3) for r in range(4)]
     ph, pp = sde_weights(g, G, k3, n3, kp3, np3, q3, m3)
     tot = (ph * (dF[D] - dF[M]) + pp * (dF[S] + dF[T_])).sum(axis=(0, 2))  # over q and k'
     pref = -(p.U / 4.0) * (g.T / g.nk) ** 2
     out = np.zeros((g.nk, p.n_ext), dtype=np.complex128)
-    out[kk, kn - g.e_lo] = pref * tot
+    out[kk[ks], kn[ks] - g.e_lo] = pref * tot
     return out
 
 
