@@ -131,6 +131,13 @@ PQ_API pq_status pq_get_Phi(const pq_ctx *ctx, int channel, int Q, double *out, 
  * (App. A, "Notations": chi from F and the bare bubble). */
 PQ_API pq_status pq_get_chi(const pq_ctx *ctx, int channel, double *out, size_t len);
 
+/* Second-order self-energy Sigma~1 = -U^2 FFT^-1[G^2(r) G(-r)] (Sec. II.B:
+ * the self-energy of the second-order diagram, summed over all frequencies
+ * in imaginary time) of G = [G0^-1 - Sigma]^-1 for the given Sigma, host c128
+ * [L*L][n_ext] (NULL = the current state), written to out, host c128
+ * [L*L][n_ext] (len = doubles available).  The state is not changed. */
+PQ_API pq_status pq_sigma_second_order(pq_ctx *ctx, const double *sigma_c128, double *out, size_t len);
+
 /* Replace the state: Phi as host c128 [4][N_Q][n][n] (converted to the
  * storage precision) and Sigma as host c128 [L*L][n_ext]; either may be NULL
  * to keep it. */

@@ -35,6 +35,10 @@ the design notes):
     two outer stored frequencies (momentum averaged).
   * Jacobi update from the state (Phi, Sigma), linear mixing of both.
 
+Parity unpinned: chi_s and chi_t (the pp-channel susceptibilities have no
+closed form or printed value to check against; chi_d and chi_m are pinned by
+the first-order RPA expansion).
+
 Array layout: Phi[r, Q, k, k'] with r in (d, m, s, t), Q = iq*NOmega + (m-m_lo),
 k = ik*Nnu + (n-n_lo); Sigma[ik, n-e_lo] on the extended range.
 """

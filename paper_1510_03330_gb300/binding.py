@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = C.c_int
     lib.pq_get_chi.argtypes = [P, C.c_int, D, C.c_size_t]
     lib.pq_get_chi.restype = C.c_int
+    lib.pq_sigma_second_order.argtypes = [P, D, D, C.c_size_t]
+    lib.pq_sigma_second_order.restype = C.c_int
     lib.pq_set_state.argtypes = [P, D, D]
     lib.pq_set_state.restype = C.c_int
     lib.pq_get_sizes.argtypes = [P, C.POINTER(C.c_longlong)]
@@ -218,6 +220,18 @@ class Solver:
     def chi(self, channel: int) -> np.ndarray:
         out = np.empty(self.p.n_Q, dtype=np.complex128)
         self._check(self.lib.pq_get_chi(self.h, channel, _dptr(out), out.size * 2))
+        return out
+
+    def sigma_second_order(self, sigma: np.ndarray | None = None) -> np.ndarray:
+        """Second-order self-energy (the paper's Sigma~1) of G[sigma] (default: the state)."""
+        p = self.p
+        out = np.empty((p.n_k, p.n_ext), dtype=np.complex128)
+        sa = None
+        if sigma is not None:
+            sa = np.ascontiguousarray(sigma, dtype=np.complex128)
+            assert sa.shape == (p.n_k, p.n_ext)
+        self._check(self.lib.pq_sigma_second_order(self.h, _dptr(sa) if sa is not None else None, _dptr(out),
+                                                   out.size * 2))
         return out
 
     def set_state(self, phi: np.ndarray | None = None, sigma: np.ndarray | None = None):

@@ -144,7 +144,7 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
   mark(2);
   CK(pq::launch_kernels_extract(st, g, b, c->c64));
   mark(3);
-  CK(pq::launch_sigma1(st, g, c->z, b));
+  CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
   mark(4);
   CK(pq::launch_sigma2(st, g, c->z, b));
   mark(5);
@@ -300,7 +300,9 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.s2_cph, cs * 2 * g.nQ * (size_t)n_nu},
       {(void **)&b.s2_cpp, cs * g.nQ * (size_t)n_nu},
       {(void **)&b.chi, cs * 4 * g.nQ},
+      {(void **)&b.gemm_work, cs * 64 * (size_t)g.nk * std::max(z.ntau, g.n_ext)},
   };
+  b.gemm_work_elems = 64LL * g.nk * std::max(z.ntau, g.n_ext);
   size_t need = 0;
   for (auto &r : reqs) need += (r.bytes + 255) & ~(size_t)255;
   for (auto &r : reqs) {
@@ -452,6 +454,26 @@ pq_status pq_get_chi(const pq_ctx *cc, int channel, double *out, size_t len) {
   CK(pq::launch_chi(c->st, c->g, c->b, c->c64));
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(out, c->b.chi + (size_t)channel * c->g.nQ, sizeof(double2) * c->g.nQ, cudaMemcpyDeviceToHost));
+  return PQ_OK;
+}
+
+pq_status pq_sigma_second_order(pq_ctx *c, const double *sigma_c128, double *out, size_t len) {
+  if (!c || !out) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  const size_t need = (size_t)2 * c->g.nk * c->g.n_ext;
+  if (len < need) return fail(c, PQ_EINVAL, "Sigma~1 needs %zu doubles, got %zu", need, len);
+  pq::Buffers &b = c->b;
+  const double2 *src = b.sigma;
+  CK(cudaStreamSynchronize(c->st));
+  if (sigma_c128) {
+    // the last Sigma_new is informational only, so its buffer stages the input
+    CK(cudaMemcpy(b.sigma_new, sigma_c128, need * sizeof(double), cudaMemcpyHostToDevice));
+    src = b.sigma_new;
+  }
+  CK(pq::launch_tail_c1(c->st, c->g, src, b.scal + 3));
+  CK(pq::launch_sigma1(c->st, c->g, c->z, pq::sigma1_args(b, src, b.scal + 3, b.sigma1)));
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(out, b.sigma1, need * sizeof(double), cudaMemcpyDeviceToHost));
   return PQ_OK;
 }
 

@@ -13,16 +13,26 @@ namespace pq {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
+// kchunk > 0: split-K, blockIdx.z = split index, the split covers
+// k in [z*kchunk, min(K, (z+1)*kchunk)) and writes its partial to C + z*sC.
 __global__ void __launch_bounds__(NT) zgemm_kernel(int M, int N, int K, double2 alpha, const double2 *__restrict__ A,
                                                    int lda, long long sA, const double2 *__restrict__ B, int ldb,
-                                                   long long sB, double2 beta, double2 *C, int ldc, long long sC) {
+                                                   long long sB, double2 beta, double2 *C, int ldc, long long sC,
+                                                   int kchunk) {
   __shared__ double2 As[BK][BM];
   __shared__ double2 Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  A += blockIdx.z * sA;
-  B += blockIdx.z * sB;
+  if (kchunk > 0) {
+    const int kb = blockIdx.z * kchunk;
+    A += kb;
+    B += (long long)kb * ldb;
+    K = min(K - kb, kchunk);
+  } else {
+    A += blockIdx.z * sA;
+    B += blockIdx.z * sB;
+  }
   C += blockIdx.z * sC;
   double2 acc[4][4];
 #pragma unroll
@@ -84,7 +94,46 @@ cudaError_t zgemm_fp64(cudaStream_t st, int M, int N, int K, double2 alpha, cons
                        int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  zgemm_kernel<<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  zgemm_kernel<<<grid, NT, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 0);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void splitk_reduce(int M, int N, int splits, double2 alpha, const double2 *__restrict__ W, double2 beta,
+                              double2 *C, int ldc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int z = 0; z < splits; ++z) s = s + W[(long long)z * M * N + i];
+  double2 *cp = C + (long long)(i / N) * ldc + i % N;
+  double2 v = cmul(alpha, s);
+  if (beta.x != 0.0 || beta.y != 0.0) v = cfma(beta, *cp, v);
+  *cp = v;
+}
+}  // namespace
+
+int zgemm_splits(int M, int N, int K, long long work_elems) {
+  long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  long long want = (4 * 152 + tiles - 1) / tiles;          // about four CTAs per SM
+  long long kcap = (K + 4 * BK - 1) / (4 * BK);             // at least four k-steps per split
+  long long wcap = work_elems / ((long long)M * N);
+  long long s = want < kcap ? want : kcap;
+  if (s > wcap) s = wcap;
+  return s < 1 ? 1 : (int)s;
+}
+
+cudaError_t zgemm_fp64_splitk(cudaStream_t st, int M, int N, int K, double2 alpha, const double2 *A, int lda,
+                              const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *work,
+                              long long work_elems) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  int splits = zgemm_splits(M, N, K, work_elems);
+  if (splits <= 1) return zgemm_fp64(st, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
+  int kchunk = (K + splits - 1) / splits;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+  zgemm_kernel<<<grid, NT, 0, st>>>(M, N, K, make_double2(1.0, 0.0), A, lda, 0, B, ldb, 0, make_double2(0.0, 0.0),
+                                    work, N, (long long)M * N, kchunk);
+  splitk_reduce<<<(M * N + 255) / 256, 256, 0, st>>>(M, N, splits, alpha, work, beta, C, ldc);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,20 @@ struct Buffers {
   double2 *s2_cph = nullptr;     // [2][nQ][n_nu] C-weighted ph tables (d-m, m)
   double2 *s2_cpp = nullptr;     // [nQ][n_nu] C-weighted pp table (s+t)
   double2 *chi = nullptr;        // [4][nQ]
+  double2 *gemm_work = nullptr;  // split-K partials of the Sigma~1 transforms
+  long long gemm_work_elems = 0;
+};
+
+// Pointers of one Sigma~1 evaluation (the context's buffers, or a caller's scratch).
+struct Sigma1Args {
+  const double2 *sigma;  // [nk][n_ext] input self-energy
+  double *c1;            // device scalar: c1 of its 1/(i nu) tail (written)
+  double2 *out;          // [nk][n_ext] Sigma~1
+  double2 *R, *gkt, *grt, *srn;
+  const double2 *E, *Ef, *ph, *phc;
+  const double *tau;
+  double2 *work;
+  long long work_elems;
 };
 
 struct Sizes {
@@ -48,6 +62,10 @@ struct Sizes {
   int j_lo, nj; // frequency range of the Sigma~2 bubble tables
 };
 
+int zgemm_splits(int M, int N, int K, long long work_elems);
+cudaError_t zgemm_fp64_splitk(cudaStream_t st, int M, int N, int K, double2 alpha, const double2 *A, int lda,
+                              const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *work,
+                              long long work_elems);
 cudaError_t zgemm_fp64(cudaStream_t st, int M, int N, int K, double2 alpha, const double2 *A, int lda, long long sA,
                        const double2 *B, int ldb, long long sB, double2 beta, double2 *C, int ldc, long long sC,
                        int batch);
@@ -55,7 +73,9 @@ cudaError_t zgemm_fp64(cudaStream_t st, int M, int N, int K, double2 alpha, cons
 // one-particle steps (pq_onebody.cu)
 cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b);
 cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b);
-cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);
+cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const Sigma1Args &a);
+Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *out);
+cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1);
 cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b);
 cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
 

@@ -77,12 +77,12 @@ __device__ inline void tail_moments(const Grid &g, double c1, int ik, double &c2
 }
 
 // Matsubara remainders R(k, n) = G(k, n) - tails, n in [-M, M-1].
-__global__ void s1_remainder_kernel(Grid g, int M, const double2 *__restrict__ sigma, const double *__restrict__ scal,
+__global__ void s1_remainder_kernel(Grid g, int M, const double2 *__restrict__ sigma, const double *__restrict__ c1p,
                                     double2 *__restrict__ R) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nk * 2 * M) return;
   int ik = i / (2 * M), n = -M + i % (2 * M);
-  double c1 = scal[0], c2, c3;
+  double c1 = c1p[0], c2, c3;
   tail_moments(g, c1, ik, c2, c3);
   double2 G = cinv(g0_inverse(g, ik, n) - sigma_at(g, sigma, c1, ik, n));
   double nu = nu_of(g, n);
@@ -93,13 +93,13 @@ __global__ void s1_remainder_kernel(Grid g, int M, const double2 *__restrict__ s
 
 // G(k, tau) += analytic transforms of the subtracted tails (0 < tau < beta):
 // 1/(i nu) -> -1/2, 1/(i nu)^2 -> tau/2 - beta/4, 1/(i nu)^3 -> tau (beta - tau)/4.
-__global__ void s1_tails_kernel(Grid g, int ntau, const double *__restrict__ tau, const double *__restrict__ scal,
+__global__ void s1_tails_kernel(Grid g, int ntau, const double *__restrict__ tau, const double *__restrict__ c1p,
                                 double2 *__restrict__ gkt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nk * ntau) return;
   int ik = i / ntau, j = i % ntau;
   double c2, c3;
-  tail_moments(g, scal[0], ik, c2, c3);
+  tail_moments(g, c1p[0], ik, c2, c3);
   double t = tau[j], b = g.beta;
   gkt[i].x += -0.5 + c2 * (0.5 * t - 0.25 * b) + c3 * t * (b - t) * 0.25;
 }
@@ -188,22 +188,49 @@ cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b) {
+Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *out) {
+  Sigma1Args a;
+  a.sigma = sigma;
+  a.c1 = c1;
+  a.out = out;
+  a.R = b.s1_R;
+  a.gkt = b.s1_gkt;
+  a.grt = b.s1_grt;
+  a.srn = b.s1_srn;
+  a.E = b.s1_E;
+  a.Ef = b.s1_Ef;
+  a.ph = b.s1_ph;
+  a.phc = b.s1_phc;
+  a.tau = b.s1_tau;
+  a.work = b.gemm_work;
+  a.work_elems = b.gemm_work_elems;
+  return a;
+}
+
+cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1) {
+  tail_c1_kernel<<<1, 256, 0, st>>>(g, sigma, c1);
+  return cudaGetLastError();
+}
+
+// Sigma~1 from the given self-energy (its tail coefficient c1 already in a.c1):
+// R = G - tails; G(k,tau) = T R E + tails(tau); G(r,tau) = ph G(k,tau);
+// Sigma(r,tau) = U^2 G(r,tau)^2 G(-r,beta-tau); Sigma(r,nu) = Sigma(r,tau) Ef; Sigma~1 = phc Sigma(r,nu).
+cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const Sigma1Args &a) {
   const int M = z.M, nt = z.ntau;
-  s1_remainder_kernel<<<nblk((long long)g.nk * 2 * M, 256), 256, 0, st>>>(g, M, b.sigma, b.scal, b.s1_R);
-  cudaError_t e = zgemm_fp64(st, g.nk, nt, 2 * M, make_double2(g.T, 0.0), b.s1_R, 2 * M, 0, b.s1_E, nt, 0,
-                             make_double2(0.0, 0.0), b.s1_gkt, nt, 0, 1);
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  s1_remainder_kernel<<<nblk((long long)g.nk * 2 * M, 256), 256, 0, st>>>(g, M, a.sigma, a.c1, a.R);
+  cudaError_t e = zgemm_fp64_splitk(st, g.nk, nt, 2 * M, make_double2(g.T, 0.0), a.R, 2 * M, a.E, nt, zero, a.gkt,
+                                    nt, a.work, a.work_elems);
   if (e != cudaSuccess) return e;
-  s1_tails_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, b.s1_tau, b.scal, b.s1_gkt);
-  e = zgemm_fp64(st, g.nk, nt, g.nk, make_double2(1.0, 0.0), b.s1_ph, g.nk, 0, b.s1_gkt, nt, 0,
-                 make_double2(0.0, 0.0), b.s1_grt, nt, 0, 1);
+  s1_tails_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, a.tau, a.c1, a.gkt);
+  e = zgemm_fp64_splitk(st, g.nk, nt, g.nk, one, a.ph, g.nk, a.gkt, nt, zero, a.grt, nt, a.work, a.work_elems);
   if (e != cudaSuccess) return e;
-  s1_product_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, b.s1_grt, b.s1_gkt);
-  e = zgemm_fp64(st, g.nk, g.n_ext, nt, make_double2(1.0, 0.0), b.s1_gkt, nt, 0, b.s1_Ef, g.n_ext, 0,
-                 make_double2(0.0, 0.0), b.s1_srn, g.n_ext, 0, 1);
+  s1_product_kernel<<<nblk((long long)g.nk * nt, 256), 256, 0, st>>>(g, nt, a.grt, a.gkt);
+  e = zgemm_fp64_splitk(st, g.nk, g.n_ext, nt, one, a.gkt, nt, a.Ef, g.n_ext, zero, a.srn, g.n_ext, a.work,
+                        a.work_elems);
   if (e != cudaSuccess) return e;
-  e = zgemm_fp64(st, g.nk, g.n_ext, g.nk, make_double2(1.0, 0.0), b.s1_phc, g.nk, 0, b.s1_srn, g.n_ext, 0,
-                 make_double2(0.0, 0.0), b.sigma1, g.n_ext, 0, 1);
+  e = zgemm_fp64_splitk(st, g.nk, g.n_ext, g.nk, one, a.phc, g.nk, a.srn, g.n_ext, zero, a.out, g.n_ext, a.work,
+                        a.work_elems);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

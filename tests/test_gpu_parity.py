@@ -88,3 +88,18 @@ def test_solver_reports_convergence_and_state_roundtrip():
             t.set_state(phi, sig)
             assert rel(t.sigma(), sig) == 0.0
             assert rel(all_slices(t, t.Phi, p), phi) == 0.0
+
+
+@pytest.mark.parametrize("name", ["square_3x3_nu8_om7_mu", "bethe_u1_b10"])
+def test_second_order_self_energy_matches_oracle(name):
+    """pq_sigma_second_order (the paper's Sigma~1) against the oracle's imaginary-time route."""
+    from paper_1510_03330_gb300.binding import Solver
+
+    p = CASES[name]
+    g = O.make_grid(p)
+    _, sig = random_state(p, seed=7)
+    ref = O.sigma1_second_order(g, sig)
+    with Solver(p) as s:
+        assert rel(s.sigma_second_order(sig), ref) < TOL_FP64
+        s.set_state(sigma=sig)
+        assert rel(s.sigma_second_order(), ref) < TOL_FP64

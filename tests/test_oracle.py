@@ -386,3 +386,28 @@ def test_third_order_survives_away_from_half_filling():
     base = Params("square", beta=2.5, U=1.0, mu=0.4, L=2, n_nu=6, n_Omega=5)
     r = [np.abs(_vertex_correction(base.with_(U=U))).max() / U**3 for U in (0.2, 0.1, 0.05)]
     assert max(r) < 1.03 * min(r)
+
+
+def test_susceptibility_first_order_rpa():
+    """With the first-iteration vertex F = Lambda = (U, -U, ...), chi_m = chi0 + U chi0^2 and
+    chi_d = chi0 - U chi0^2: the first-order terms of the RPA forms chi0/(1 -+ U chi0),
+    with chi0 = -(T/N) sum_k G0(k) G0(k+q) summed here with the test's own G0."""
+    p = SMALL_ODD
+    res = O.iterate(p, O.zero_state(p))
+    chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
+    L, T, N = p.L, 1.0 / p.beta, p.L * p.L
+    n_lo, m_lo = -p.n_nu // 2, -(p.n_Omega // 2)
+    for iq in range(N):
+        qx, qy = divmod(iq, L)
+        for im in range(p.n_Omega):
+            m = m_lo + im
+            b = 0.0
+            for ik in range(N):
+                kx, ky = divmod(ik, L)
+                for n in range(n_lo, n_lo + p.n_nu):
+                    b += _g0_square(p, 2 * np.pi * kx / L, 2 * np.pi * ky / L, n) * _g0_square(
+                        p, 2 * np.pi * (kx + qx) / L, 2 * np.pi * (ky + qy) / L, n + m)
+            chi0 = -T / N * b
+            Q = iq * p.n_Omega + im
+            assert abs(chi[1, Q] - (chi0 + p.U * chi0**2)) < 1e-13
+            assert abs(chi[0, Q] - (chi0 - p.U * chi0**2)) < 1e-13
