@@ -153,8 +153,35 @@ PQ_API pq_status pq_get_sizes(const pq_ctx *ctx, long long *out8);
 PQ_API pq_status pq_step_times(const pq_ctx *ctx, float *out, int n);
 PQ_API const char *pq_step_name(int i);
 
-/* Message of the last failure on ctx (or of the last failed pq_init when
- * ctx is NULL). */
+/* Second-order self-energy without device allocation, for callers that
+ * cannot call cudaMalloc: a host program that has handed all device memory
+ * to its own allocator, or a plug-in called inside another solver's loop
+ * where an allocation (and the device synchronisation it implies) is not
+ * allowed.  The paper has no counterpart; this is the Sigma~1 of
+ * pq_sigma_second_order computed without a context.
+ *   sigma_dev: device c128 [L*L][n_omega+n_nu-1], the self-energy of G (read);
+ *   out_dev:   device c128 [L*L][n_omega+n_nu-1], Sigma~1 (written);
+ *   the other arguments are those of pq_init and pq_options; cuda_stream is
+ *   a cudaStream_t (NULL = legacy default stream).
+ * Work is queued on cuda_stream and the call returns without waiting: out_dev
+ * is ready when the stream reaches that point.  All intermediates live in one
+ * static device array of 6.73 MB that every GPU which loads the library holds
+ * until the process exits; sizes beyond it are rejected with PQ_EINVAL:
+ * L*L <= 16, 2*tau_matsubara <= 512, tau_panels*tau_order <= 512,
+ * n_omega+n_nu-1 <= 128, tau_order <= 32.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves its contents behind; each call writes every element it
+ * reads before reading it, so nothing has to be cleared, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it.
+ * Errors: PQ_EINVAL, PQ_ECUDA; pq_last_error(NULL) gives the message. */
+PQ_API pq_status pq_sigma_second_order_noalloc(int lattice, double beta, double U, double mu, double hop,
+                                               int L, int n_nu, int n_omega, int tau_panels, int tau_order,
+                                               int tau_matsubara, const double *sigma_dev, double *out_dev,
+                                               void *cuda_stream);
+
+/* Message of the last failure on ctx (or, when ctx is NULL, of the last
+ * failed call that has no context: pq_init or pq_sigma_second_order_noalloc). */
 PQ_API const char *pq_last_error(const pq_ctx *ctx);
 
 /* Release the context and its device memory.  NULL is a no-op. */

@@ -83,6 +83,9 @@ def load_library(path: str = LIB_PATH):
     lib.pq_get_chi.restype = C.c_int
     lib.pq_sigma_second_order.argtypes = [P, D, D, C.c_size_t]
     lib.pq_sigma_second_order.restype = C.c_int
+    lib.pq_sigma_second_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                  C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
+    lib.pq_sigma_second_order_noalloc.restype = C.c_int
     lib.pq_set_state.argtypes = [P, D, D]
     lib.pq_set_state.restype = C.c_int
     lib.pq_get_sizes.argtypes = [P, C.POINTER(C.c_longlong)]

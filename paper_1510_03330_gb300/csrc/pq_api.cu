@@ -176,6 +176,11 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
 
 }  // namespace
 
+namespace pq {
+// Message for pq_last_error(NULL) from a call that has no context.
+void set_context_free_error(const char *msg) { g_init_err = msg; }
+}  // namespace pq
+
 extern "C" {
 
 void pq_default_options(pq_options *o) {
