@@ -34,8 +34,8 @@ from paper_1510_03330_gb300.workloads import CONFIGS, FP64, SPLIT_BF16X3, SPLIT_
 
 METRIC = "parquet iter/s and BSE TFLOP/s: split-precision vs FP64 path at a stated Σ error"
 UNIT = "iter/s"
-DEFAULT_WORKLOAD = "square4_u2_b5"
-DEFAULT_PRECISION = FP64
+DEFAULT_WORKLOAD = "square8_u2_b4"
+DEFAULT_PRECISION = SPLIT_TF32X3
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
 LAUNCHES_PER_ITER = 18
@@ -198,6 +198,8 @@ def main():
                     choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_BF16X6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64 run that states the split path's error and the FP64 iteration rate")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -242,7 +244,37 @@ def main():
         if dist:
             dist.barrier()
 
+    compare = None
+    if a.precision != FP64 and not a.no_fp64_compare:
+        # FP64 path alongside: two iterations from the zero state; the split run below starts the
+        # same way, so its Sigma, F and chi_m after two iterations are compared with these
+        ref = Solver(p, precision=FP64, time_steps=True)
+        ref.iterate(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ref.iterate(1)
+        torch.cuda.synchronize()
+        fp64_s = time.perf_counter() - t0
+        fp64_bse_ms = ref.step_times()["bse"]
+        ref_sig, ref_F, ref_chi = ref.sigma(), ref.F(1, p.n_Q // 2), ref.chi(1)
+        ref.close()
+        del ref
+        torch.cuda.empty_cache()
+        compare = {"fp64_iter_per_s": 1.0 / fp64_s,
+                   "fp64_bse_tflops": 8.0 * p.n**3 * 4 * p.n_Q / (fp64_bse_ms * 1e-3) / 1e12}
+
     solver = Solver(p, precision=a.precision, time_steps=True)
+    if compare is not None:
+        solver.iterate(2)
+
+        def relerr(x, y):
+            return float(np.abs(x - y).max() / np.abs(y).max())
+
+        compare.update({"iterations": 2, "sigma_rel_err": relerr(solver.sigma(), ref_sig),
+                        "F_m_rel_err": relerr(solver.F(1, p.n_Q // 2), ref_F),
+                        "chi_m_rel_err": relerr(solver.chi(1), ref_chi),
+                        "note": "max-norm errors relative to max|FP64| after two iterations from the zero state; "
+                                "F_m at Q = N_Q/2"})
     for _ in range(a.warmup):
         solver.iterate(1)
     stream = torch.cuda.current_stream()
@@ -305,6 +337,9 @@ def main():
             "kernels": {"ms_per_iter": steps, "bse": bse_roof, "assemble": remap_roof},
             "bse_tflops": bse_tflops, "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
             "device_bytes": dev_bytes}
+    if compare is not None:
+        compare["split_over_fp64"] = value / compare["fp64_iter_per_s"]
+        line["fp64_compare"] = compare
 
     if not a.no_e2e:
         # end to end through the public API: a fresh context (set-up, table uploads), K iterations

@@ -51,7 +51,7 @@ typedef enum {
   PQ_ENOMEM = 2,   /* device allocation failed; the message gives the bytes */
   PQ_ECUDA = 3,    /* a CUDA call failed; the context is poisoned */
   PQ_ENOTCONV = 4, /* pq_iterate reached max_iter above tol (state is valid) */
-  PQ_ETIMEOUT = 5, /* reserved: a bounded device wait gave up */
+  PQ_ETIMEOUT = 5, /* a bounded device wait gave up; the context is poisoned */
   PQ_ENAN = 6,     /* a non-finite Sigma appeared; the context is poisoned */
   PQ_ESTATE = 7    /* the context is poisoned by an earlier PQ_ECUDA/PQ_ENAN */
 } pq_status;
@@ -60,8 +60,10 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
 
 /* Arithmetic of the vertex storage and the BSE products.
  * PQ_FP64: complex128 vertices, FP64 everywhere.
- * PQ_SPLIT_*: complex64 vertices; the BSE runs on the tensor cores as a
- * split-operand product with FP32 accumulation; Dyson, K1/K2, Sigma stay FP64. */
+ * PQ_SPLIT_*: complex64 vertices, parquet assembly in FP32; the BSE runs on the
+ * tensor cores as a split-operand product with FP32 accumulation; Dyson,
+ * K1/K2 and the Sigma sums stay FP64.  PQ_SPLIT_TF32X3 is available; the BF16
+ * variants are rejected by pq_init with PQ_EINVAL in this build. */
 typedef enum {
   PQ_FP64 = 0,
   PQ_SPLIT_TF32X3 = 1,

@@ -158,12 +158,19 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
                       (const double2 *)b.fv, g.n, nn * nn, make_double2(1.0 - g.mix, 0.0), (double2 *)b.phi, g.n,
                       nn * nn, 4 * g.nQ));
   } else {
-    return fail(c, PQ_EINVAL, "split-precision BSE not available in this build");
+    CK(pq::launch_bse_tf32x3(st, g.n, 4 * g.nQ, (const float2 *)b.gam, (const float2 *)b.fv, (float2 *)b.phi,
+                             (float)g.mix, (int *)(b.scal + 4)));
   }
   mark(8);
-  double h[3];
+  double h[5];
   CK(cudaMemcpyAsync(h, b.scal, sizeof h, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  int timeout_flag;
+  std::memcpy(&timeout_flag, &h[4], sizeof timeout_flag);
+  if (timeout_flag) {
+    c->poisoned = true;
+    return fail(c, PQ_ETIMEOUT, "a tensor-core pipeline wait gave up; the state is invalid");
+  }
   if (tm) {
     for (int i = 0; i < PQ_NSTEPS - 1; ++i) cudaEventElapsedTime(&c->times[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&c->times[PQ_NSTEPS - 1], c->ev[0], c->ev[PQ_NSTEPS - 1]);
@@ -211,6 +218,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   if (o.tau_panels < 1 || o.tau_order < 2 || o.tau_matsubara < 1)
     return fail(nullptr, PQ_EINVAL, "bad imaginary-time quadrature sizes");
   if (o.precision < PQ_FP64 || o.precision > PQ_SPLIT_BF16X6) return fail(nullptr, PQ_EINVAL, "unknown precision");
+  if (o.precision == PQ_SPLIT_BF16X3 || o.precision == PQ_SPLIT_BF16X6)
+    return fail(nullptr, PQ_EINVAL, "BF16 split products are not available in this build; use PQ_SPLIT_TF32X3");
   if (!(o.mix_alpha > 0.0 && o.mix_alpha <= 1.0)) return fail(nullptr, PQ_EINVAL, "mix_alpha must be in (0, 1]");
   if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
     return fail(nullptr, PQ_EINVAL, "dev_alloc and dev_free must be given together");

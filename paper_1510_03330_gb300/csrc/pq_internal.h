@@ -24,7 +24,8 @@ struct Buffers {
   double2 *k2row = nullptr;      // [4][n][nQ]  (row leg k major, transfer fastest)
   double2 *k2col = nullptr;      // [4][n][nQ]
   double2 *dfpart = nullptr;     // [n][nk] dF part of Sigma, one partial per (k, k'-momentum)
-  double *scal = nullptr;        // [0] c1 of the Sigma tail, [1] max |dSigma| bits, [2] non-finite flag
+  double *scal = nullptr;        // [0] c1 of the Sigma tail, [1] max |dSigma| bits, [2] non-finite flag,
+                                 // [3] c1 scratch of pq_sigma_second_order, [4] tensor-core wait timeout flag
   // Sigma~1 in imaginary time
   double2 *s1_R = nullptr;       // [nk][2M] Matsubara remainders
   double2 *s1_E = nullptr;       // [2M][ntau] exp(-i nu_n tau_j)
@@ -83,6 +84,11 @@ cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
 cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64, const double *lam4);
 size_t assemble_smem_bytes(const Grid &g, bool c64);
+
+// split-precision BSE on the tensor cores (pq_gemm_tc.cu)
+size_t bse_tc_smem_bytes();
+cudaError_t launch_bse_tf32x3(cudaStream_t st, int n, int batch, const float2 *A, const float2 *B, float2 *Phi,
+                              float alpha, int *err);
 
 // Sigma~2 (pq_sigma2.cu)
 cudaError_t launch_sigma2(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);

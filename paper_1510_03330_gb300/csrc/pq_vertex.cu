@@ -100,9 +100,12 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
                                                        Lam lam) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.n_om * g.n_nu;
+  // R blocks are read along columns (map A) and anti-diagonals (map C): rows padded by two
+  // elements keep both strides off the shared-memory bank period
+  const int RS = g.n_nu + 2;
   S *Rd = (S *)smem_raw;
-  S *Rm = Rd + NB;
-  S *Pd = Rm + NB;
+  S *Rm = Rd + g.n_om * RS;
+  S *Pd = Rm + g.n_om * RS;
   S *Pm = Pd + NB;
   S *Ss = Pm + NB;
   S *St = Ss + NB;
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const long long rrow = ((long long)(tmom * g.n_om + mt) * nn + k) * nn + cmom * g.n_nu + c;
       const long long prow = ((long long)(iq * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
       const long long srow = ((long long)(iqp * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
-      Rd[e] = phi[rrow];
-      Rm[e] = phi[chan + rrow];
+      Rd[mt * RS + c] = phi[rrow];
+      Rm[mt * RS + c] = phi[chan + rrow];
       Pd[e] = phi[prow];
       Pm[e] = phi[chan + prow];
       Ss[e] = phi[2 * chan + srow];
@@ -159,8 +162,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const int nc = n + m;  // column k + q of map A
       if (inT) {
         if (nc >= g.n_lo && nc <= g.n_hi) {
-          Ad = to_c<S, C>(Rd[ti * g.n_nu + nc - g.n_lo]);
-          Am = to_c<S, C>(Rm[ti * g.n_nu + nc - g.n_lo]);
+          Ad = to_c<S, C>(Rd[ti * RS + nc - g.n_lo]);
+          Am = to_c<S, C>(Rm[ti * RS + nc - g.n_lo]);
         } else {
           Ad = FKd[ti];
           Am = FKm[ti];
@@ -192,8 +195,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const int nc2 = m - np_ - 1;  // column q' - k' of map C
       if (inT) {
         if (nc2 >= g.n_lo && nc2 <= g.n_hi) {
-          Cd = to_c<S, C>(Rd[ti * g.n_nu + nc2 - g.n_lo]);
-          Cm = to_c<S, C>(Rm[ti * g.n_nu + nc2 - g.n_lo]);
+          Cd = to_c<S, C>(Rd[ti * RS + nc2 - g.n_lo]);
+          Cm = to_c<S, C>(Rm[ti * RS + nc2 - g.n_lo]);
         } else {
           Cd = FKd[ti];
           Cm = FKm[ti];
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
 
 size_t assemble_smem_bytes(const Grid &g, bool c64) {
   size_t es = c64 ? sizeof(float2) : sizeof(double2);
-  return 6 * (size_t)g.n_om * g.n_nu * es + 2 * (size_t)g.n_om * es;
+  return (2 * (size_t)g.n_om * (g.n_nu + 2) + 4 * (size_t)g.n_om * g.n_nu + 2 * (size_t)g.n_om) * es;
 }
 
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64) {

@@ -18,7 +18,10 @@ CASES = {
     "square_2x2_nu6_om5": Params("square", beta=2.5, U=1.2, mu=0.0, L=2, n_nu=6, n_Omega=5),
     "square_3x3_nu8_om7_mu": Params("square", beta=2.0, U=1.0, mu=0.3, L=3, n_nu=8, n_Omega=7, hop=0.8),
     "bethe_u1_b10": CONFIGS["bethe_u1_b10"],
+    "square_3x3_nu16_om8": Params("square", beta=3.0, U=1.6, mu=0.0, L=3, n_nu=16, n_Omega=8),
+    "square_1x1_nu6_om5": Params("square", beta=2.0, U=1.0, mu=0.2, L=1, n_nu=6, n_Omega=5, hop=0.5),
 }
+TOL_SPLIT = 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -103,3 +106,39 @@ def test_second_order_self_energy_matches_oracle(name):
         assert rel(s.sigma_second_order(sig), ref) < TOL_FP64
         s.set_state(sigma=sig)
         assert rel(s.sigma_second_order(), ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", ["square_2x2_nu8_om8", "square_3x3_nu8_om7_mu", "bethe_u1_b10",
+                                  "square_3x3_nu16_om8", "square_1x1_nu6_om5"])
+def test_split_tf32x3_iterations_match_oracle(name):
+    """Split path (complex64 vertices, TF32x3 tensor-core BSE) against the FP64
+    oracle after three iterations from zero and one from a seeded state: Sigma,
+    F and chi within 1e-6; the raw BSE output Phi, whose k''-sums cancel, within
+    5e-6 (TF32x3 keeps ~2^-22 per product)."""
+    from paper_1510_03330_gb300.binding import Solver
+    from paper_1510_03330_gb300.workloads import SPLIT_TF32X3
+
+    p = CASES[name]
+    st = O.zero_state(p)
+    errs = {}
+    with Solver(p, precision=SPLIT_TF32X3) as s:
+        for it in range(3):
+            res = O.iterate(p, st)
+            st = res.state
+            s.iterate(1)
+            errs[f"sigma{it}"] = rel(s.sigma(), st.sigma)
+        errs["phi"] = rel(all_slices(s, s.Phi, p), st.phi)
+        errs["F"] = rel(all_slices(s, s.F, p), res.F)
+        chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
+        errs["chi_m"] = rel(s.chi(1), chi[1])
+    phi, sig = random_state(p, seed=1510)
+    res = O.iterate(p, O.State(phi, sig))
+    with Solver(p, precision=SPLIT_TF32X3) as s:
+        s.set_state(phi, sig)
+        s.iterate(1)
+        errs["sigma_rand"] = rel(s.sigma(), res.state.sigma)
+        errs["phi_rand"] = rel(all_slices(s, s.Phi, p), res.state.phi)
+        errs["F_rand"] = rel(all_slices(s, s.F, p), res.F)
+    print(name, errs)
+    assert max(v for k, v in errs.items() if not k.startswith("phi")) < TOL_SPLIT, errs
+    assert max(v for k, v in errs.items() if k.startswith("phi")) < 5 * TOL_SPLIT, errs
