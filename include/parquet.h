@@ -62,8 +62,9 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
  * PQ_FP64: complex128 vertices, FP64 everywhere.
  * PQ_SPLIT_*: complex64 vertices, parquet assembly in FP32; the BSE runs on the
  * tensor cores as a split-operand product with FP32 accumulation; Dyson,
- * K1/K2 and the Sigma sums stay FP64.  PQ_SPLIT_TF32X3 is available; the BF16
- * variants are rejected by pq_init with PQ_EINVAL in this build. */
+ * K1/K2 and the Sigma sums stay FP64.  PQ_SPLIT_TF32X3 (TF32 hi/lo,
+ * ~2^-22 per product) and PQ_SPLIT_BF16X3 (BF16 hi/lo, ~2^-16, twice the K per
+ * stage) are available; PQ_SPLIT_BF16X6 is rejected by pq_init with PQ_EINVAL. */
 typedef enum {
   PQ_FP64 = 0,
   PQ_SPLIT_TF32X3 = 1,

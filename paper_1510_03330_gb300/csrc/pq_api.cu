@@ -158,8 +158,9 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
                       (const double2 *)b.fv, g.n, nn * nn, make_double2(1.0 - g.mix, 0.0), (double2 *)b.phi, g.n,
                       nn * nn, 4 * g.nQ));
   } else {
-    CK(pq::launch_bse_tf32x3(st, g.n, 4 * g.nQ, (const float2 *)b.gam, (const float2 *)b.fv, (float2 *)b.phi,
-                             (float)g.mix, (int *)(b.scal + 4)));
+    CK(pq::launch_bse_split(st, c->opt.precision == PQ_SPLIT_BF16X3 ? 1 : 0, g.n, 4 * g.nQ,
+                            (const float2 *)b.gam, (const float2 *)b.fv, (float2 *)b.phi, (float)g.mix,
+                            (int *)(b.scal + 4)));
   }
   mark(8);
   double h[5];
@@ -218,8 +219,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   if (o.tau_panels < 1 || o.tau_order < 2 || o.tau_matsubara < 1)
     return fail(nullptr, PQ_EINVAL, "bad imaginary-time quadrature sizes");
   if (o.precision < PQ_FP64 || o.precision > PQ_SPLIT_BF16X6) return fail(nullptr, PQ_EINVAL, "unknown precision");
-  if (o.precision == PQ_SPLIT_BF16X3 || o.precision == PQ_SPLIT_BF16X6)
-    return fail(nullptr, PQ_EINVAL, "BF16 split products are not available in this build; use PQ_SPLIT_TF32X3");
+  if (o.precision == PQ_SPLIT_BF16X6)
+    return fail(nullptr, PQ_EINVAL, "BF16x6 split products are not available in this build");
   if (!(o.mix_alpha > 0.0 && o.mix_alpha <= 1.0)) return fail(nullptr, PQ_EINVAL, "mix_alpha must be in (0, 1]");
   if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
     return fail(nullptr, PQ_EINVAL, "dev_alloc and dev_free must be given together");

@@ -3,9 +3,10 @@
 // For every (r, Q) the BSE (App. A, Eq. PA_F_Phi) is one complex n x n x n
 // product C = A B with A = s_r Gamma_r(Q) diag(X_r(Q)) and B = F_r(Q), both
 // complex64, and the mixing Phi <- alpha C + (1 - alpha) Phi in the epilogue.
-// Each FP32 operand x is split into TF32 parts x = h + l (h = tf32(x),
-// l = tf32(x - h)); a real product X Y is taken as Xh Yh + Xh Yl + Xl Yh with
-// FP32 accumulation (the TF32x3 scheme, ~2^-22 relative per product).
+// Each FP32 operand x is split into low-precision parts and a real product X Y
+// is taken over the leading part products, with FP32 accumulation:
+//   TF32x3: x = h + l (TF32), XY ~ Xh Yh + Xh Yl + Xl Yh          (~2^-22 per product)
+//   BF16x3: x = h + l (BF16), same three products                  (~2^-16 per product)
 //
 // Complex arithmetic as two real products into one 128 x 256 accumulator:
 // the B tile is staged as 384 K-major rows [-Bi ; Br ; Bi], so
@@ -14,12 +15,14 @@
 // leaves Re C in accumulator columns 0..127 and Im C in 128..255.
 //
 // One CTA owns a 128 x 128 complex output tile in tensor memory (columns
-// 0..255).  All 256 threads convert and stage the operands: the four A split
-// planes go from registers straight into tensor memory (tcgen05.st, columns
-// 256.. per stage), so the MMAs read A from tensor memory and only B from
-// swizzled shared memory -- shared-memory bandwidth is the limit of a TF32
-// product otherwise.  One thread issues the MMAs; tcgen05.commit releases each
-// of the three stages back to the producers.
+// 0..255).  The A split planes go from registers straight into tensor memory
+// (tcgen05.st), so the MMAs read A there and only B from 64-byte-swizzled
+// shared memory.  Eight producer warps fetch raw complex64 tiles with cp.async,
+// convert them and stage the planes; one warp issues the MMAs; stages hand
+// over through mbarriers, and tcgen05.commit releases each stage.  Both
+// schemes use 64-byte operand rows: 16 k per stage for TF32, 32 for BF16.
+#include <cuda_bf16.h>
+
 #include "pq_common.cuh"
 #include "pq_internal.h"
 #include "pq_tc.cuh"
@@ -28,45 +31,94 @@ namespace pq {
 
 namespace {
 
-constexpr int BM = 128, BNC = 128, BK = 16, NT = 256;
-constexpr int B_PLANE = 3 * BNC * 64;   // 384 rows x 64 B
-constexpr int STAGE = 2 * B_PLANE;      // Bh Bl
-constexpr int NSTAGE = 2;               // split stages (B planes in shared memory, A planes in TMEM)
-constexpr int RAW_A = BM * 128;         // raw complex64 A tile: 128 rows x 16 values, 16-byte chunks XOR-swizzled
-constexpr int RAW_B_ROW = BNC * 8 + 16; // raw B tile row (128 values) padded by 16 bytes
-constexpr int RAW_B = BK * RAW_B_ROW;
-constexpr int RAW = RAW_A + RAW_B;
-constexpr int NRAW = 3;                 // raw stages: cp.async runs two stages ahead
-constexpr uint32_t D_COLS = 2 * BNC;    // accumulator: Re in 0..127, Im in 128..255
-constexpr uint32_t A_STAGE_COLS = 4 * BK;  // Arh Arl Aih Ail, BK columns each
+constexpr int BM = 128, BNC = 128, NT = 256;
+constexpr int B_BLOCK = BNC * 64;        // 128 K-major rows x 64 B
+constexpr int B_PLANE = 3 * B_BLOCK;     // rows [-Bi ; Br ; Bi]
+constexpr int NSTAGE = 2;                // split stages (B planes in shared memory, A planes in TMEM)
+constexpr uint32_t D_COLS = 2 * BNC;     // accumulator: Re in 0..127, Im in 128..255
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t WAIT_TRIES = 1u << 24;
+
+enum Scheme { TF32X3 = 0, BF16X3 = 1 };
+
+template <int SC>
+struct Traits;
+template <>
+struct Traits<TF32X3> {
+  static constexpr int BK = 16;    // complex k per stage (16 x 4 B = one 64-byte row)
+  static constexpr int KG = 4;     // k per 16-byte chunk of a staged row
+  static constexpr int NRAW = 3;   // raw stages: cp.async two stages ahead
+  static constexpr uint32_t IDESC = tc::idesc_tf32(BM, 2 * BNC, false);
+};
+template <>
+struct Traits<BF16X3> {
+  static constexpr int BK = 32;    // 32 x 2 B = one 64-byte row
+  static constexpr int KG = 8;
+  static constexpr int NRAW = 2;   // one stage ahead (shared memory holds two 64 KB raw stages)
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * BNC >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);  // F32 accumulate, BF16 A and B
+};
+
+template <int SC>
+struct Layout {
+  static constexpr int BK = Traits<SC>::BK;
+  static constexpr int STAGE = 2 * B_PLANE;            // Bh, Bl
+  static constexpr int RAW_A_ROW = BK * 8;             // complex64 bytes per raw A row
+  static constexpr int RAW_A = BM * RAW_A_ROW;
+  static constexpr int RAW_B_ROW = BNC * 8 + 16;       // padded by 16 bytes
+  static constexpr int RAW_B = BK * RAW_B_ROW;
+  static constexpr int RAW = RAW_A + RAW_B;
+  static constexpr uint32_t A_PLANE_COLS = 16;         // 64 bytes of K per lane
+  static constexpr uint32_t A_STAGE_COLS = 4 * A_PLANE_COLS;  // Arh Arl Aih Ail
+  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE + (size_t)Traits<SC>::NRAW * RAW + 1024;
+};
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                : "memory");
 }
 
-__device__ __forceinline__ void split(float x, float &h, float &l) {
+__device__ __forceinline__ void split_tf32(float x, float &h, float &l) {
   h = tc::to_tf32(x);
   l = tc::to_tf32(x - h);
+}
+__device__ __forceinline__ void split_bf16(float x, float &h, float &l) {
+  h = __bfloat162float(__float2bfloat16_rn(x));
+  l = x - h;  // exact; rounded to BF16 when packed
+}
+// two consecutive-k values packed as one 32-bit word, the even k in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float even, float odd) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(even, odd);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_tmem_a(int sc, uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (sc == TF32X3) {
+    tc::mma_tf32_tmem_a(d, a, b, idesc, acc);
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
 }
 
 __device__ __forceinline__ void cp_async_mbar_arrive(void *bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(void *bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(tc::smem_u32(bar))
-               : "memory");
-}
 
 // Warp roles: warps 0..7 (256 threads) fetch, convert and stage operands and run the
 // epilogue; warp 8 allocates tensor memory and issues the MMAs.  Stages hand over through
 // mbarriers only: raw_full (cp.async landed), raw_empty (raw tile converted),
-// split_full (TF32 planes staged), split_empty (MMAs of the stage done, tcgen05.commit).
-__global__ void __launch_bounds__(NT + 32, 1) bse_tf32x3_kernel(int n, const float2 *__restrict__ A,
-                                                                const float2 *__restrict__ B, float2 *Phi,
-                                                                float alpha, int *err) {
+// split_full (split planes staged), split_empty (MMAs of the stage done, tcgen05.commit).
+template <int SC>
+__global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const float2 *__restrict__ A,
+                                                               const float2 *__restrict__ B, float2 *Phi,
+                                                               float alpha, int *err) {
+  using Tr = Traits<SC>;
+  using Ly = Layout<SC>;
+  constexpr int BK = Tr::BK, KG = Tr::KG, NRAW = Tr::NRAW;
+  constexpr bool BF = (SC == BF16X3);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t raw_full[NRAW], raw_empty[NRAW], split_full[NSTAGE], split_empty[NSTAGE], done;
@@ -101,28 +153,27 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_tf32x3_kernel(int n, const flo
 
   if (warp == 8) {
     // ---------------------------------------------------------------- MMA issuer
-    const uint32_t idesc = tc::idesc_tf32(BM, 2 * BNC, false);
     for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % NSTAGE;
       ok &= tc::mbar_wait(&split_full[s], (kt / NSTAGE) & 1, WAIT_TRIES);
       tc::fence_after_sync();
       if (lane == 0) {
-        const uint32_t bh = tc::smem_u32(sm + s * STAGE), bl = bh + B_PLANE;
-        const uint32_t a = tmem + D_COLS + (uint32_t)s * A_STAGE_COLS;
-        const uint32_t arh = a, arl = a + BK, aih = a + 2 * BK, ail = a + 3 * BK;
+        const uint32_t bh = tc::smem_u32(sm + s * Ly::STAGE), bl = bh + B_PLANE;
+        const uint32_t a = tmem + D_COLS + (uint32_t)s * Ly::A_STAGE_COLS;
+        const uint32_t arh = a, arl = a + 16, aih = a + 32, ail = a + 48;
 #pragma unroll
-        for (int j = 0; j < BK / 8; ++j) {
+        for (int j = 0; j < 2; ++j) {  // two k steps of 32 bytes per 64-byte row
           const uint32_t o = 32u * j, ak = 8u * j;
           auto d = [&](uint32_t b) { return tc::smem_desc(b + o, 16, 512, 4); };
           const uint32_t acc0 = (kt > 0 || j > 0) ? 1u : 0u;
           // D += Ar [Br | Bi]: B rows 128..383
-          tc::mma_tf32_tmem_a(tmem, arh + ak, d(bh + BNC * 64), idesc, acc0);
-          tc::mma_tf32_tmem_a(tmem, arh + ak, d(bl + BNC * 64), idesc, 1u);
-          tc::mma_tf32_tmem_a(tmem, arl + ak, d(bh + BNC * 64), idesc, 1u);
+          mma_tmem_a(SC, tmem, arh + ak, d(bh + B_BLOCK), Tr::IDESC, acc0);
+          mma_tmem_a(SC, tmem, arh + ak, d(bl + B_BLOCK), Tr::IDESC, 1u);
+          mma_tmem_a(SC, tmem, arl + ak, d(bh + B_BLOCK), Tr::IDESC, 1u);
           // D += Ai [-Bi | Br]: B rows 0..255
-          tc::mma_tf32_tmem_a(tmem, aih + ak, d(bh), idesc, 1u);
-          tc::mma_tf32_tmem_a(tmem, aih + ak, d(bl), idesc, 1u);
-          tc::mma_tf32_tmem_a(tmem, ail + ak, d(bh), idesc, 1u);
+          mma_tmem_a(SC, tmem, aih + ak, d(bh), Tr::IDESC, 1u);
+          mma_tmem_a(SC, tmem, aih + ak, d(bl), Tr::IDESC, 1u);
+          mma_tmem_a(SC, tmem, ail + ak, d(bh), Tr::IDESC, 1u);
         }
         tc::mma_commit(&split_empty[s]);
         if (kt == KT - 1) tc::mma_commit(&done);
@@ -131,38 +182,39 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_tf32x3_kernel(int n, const flo
     }
   } else {
     // ---------------------------------------------------------------- producers
-    // Operand fetch: cp.async copies the raw complex64 tiles of a stage (A: 128 rows x 128 B,
-    // B: 16 rows x 1 KB) in 16-byte chunks, eight consecutive threads per 128-byte line,
-    // NRAW - 1 stages ahead of their conversion.
+    // Operand fetch: cp.async copies the raw complex64 tiles of a stage (A: 128 rows x BK,
+    // B: BK rows x 128) in 16-byte chunks, consecutive threads along each line, NRAW - 1
+    // stages ahead of their conversion.
     // A conversion: warp w owns TMEM lanes 32(w%4).. (rows) and k half w/4; each thread
-    //    reads its row's 8 values (A chunks are XOR-swizzled by row, so 8 consecutive rows
+    //    reads its row's BK/2 values (A chunks are XOR-swizzled by row, so 8 consecutive rows
     //    hit 8 bank groups) and writes 8 columns of each of the four A planes into TMEM.
-    // B conversion: thread task (column pair p, quad kq) reads B[4kq + j][2p, 2p+1], j = 0..3
-    //    (rows padded so the two kq of an 8-lane phase fall on different bank groups) and
-    //    writes 16-byte runs of K of the six B plane rows of its two columns.
+    // B conversion: thread task (column pair p, k group g of KG values) reads KG raw rows
+    //    (padded so the two g of an 8-lane phase fall on different bank groups) and writes
+    //    one 16-byte run of K to each of the six B plane rows of its two columns.
     const int a_row = 32 * (warp & 3) + lane, a_kh = warp >> 2;
     const uint32_t a_lane = (uint32_t)(32 * (warp & 3)) << 16;
-    const int b_plo = lane & 3, b_kqlo = (lane >> 2) & 1, b_kqhi = (lane >> 3) & 1, b_phi = (lane >> 4) & 1;
-    const int b_p = b_plo + 4 * b_phi + 8 * warp, b_kq = b_kqlo + 2 * b_kqhi;
-    unsigned char *raw0 = sm + NSTAGE * STAGE;
+    const int b_plo = lane & 3, b_glo = (lane >> 2) & 1, b_ghi = (lane >> 3) & 1, b_phi = (lane >> 4) & 1;
+    const int b_p = b_plo + 4 * b_phi + 8 * warp, b_g = b_glo + 2 * b_ghi;
+    unsigned char *raw0 = sm + NSTAGE * Ly::STAGE;
+    constexpr int ACH = BK / 2;  // 16-byte chunks per raw A row
 
     auto fetch = [&](int kt) {
       const int r_ = kt % NRAW;
       if (kt >= NRAW) ok &= tc::mbar_wait(&raw_empty[r_], ((kt - NRAW) / NRAW) & 1, WAIT_TRIES);
-      unsigned char *ra = raw0 + r_ * RAW, *rb = ra + RAW_A;
+      unsigned char *ra = raw0 + r_ * Ly::RAW, *rb = ra + Ly::RAW_A;
       const int k0 = kt * BK;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < BK / 4; ++i) {
         const int e = tid + NT * i;
-        const int r = e >> 3, c = e & 7;  // A row, 16-byte chunk (2 complex values)
+        const int r = e / ACH, c = e % ACH;  // A row, 16-byte chunk (2 complex values)
         const int gr = row0 + r, k = k0 + 2 * c;
         const bool va = gr < n && k < n;
-        cp_async16(tc::smem_u32(ra + r * 128 + ((c ^ (r & 7)) << 4)),
+        cp_async16(tc::smem_u32(ra + r * Ly::RAW_A_ROW + ((c ^ (r & 7)) << 4)),
                    va ? (const void *)(A + (long long)gr * n + k) : (const void *)A, va);
         const int br = e >> 6, bc = e & 63;  // B row (k), 16-byte chunk (column pair)
         const int gk = k0 + br, col = col0 + 2 * bc;
         const bool vb = gk < n && col < n;
-        cp_async16(tc::smem_u32(rb + br * RAW_B_ROW + bc * 16),
+        cp_async16(tc::smem_u32(rb + br * Ly::RAW_B_ROW + bc * 16),
                    vb ? (const void *)(B + (long long)gk * n + col) : (const void *)B, vb);
       }
       cp_async_mbar_arrive(&raw_full[r_]);
@@ -175,62 +227,94 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_tf32x3_kernel(int n, const flo
       ok &= tc::mbar_wait(&raw_full[r_], (kt / NRAW) & 1, WAIT_TRIES);
       if (kt >= NSTAGE) ok &= tc::mbar_wait(&split_empty[s], ((kt - NSTAGE) / NSTAGE) & 1, WAIT_TRIES);
       tc::fence_after_sync();
-      const unsigned char *ra = raw0 + r_ * RAW, *rb = ra + RAW_A;
+      const unsigned char *ra = raw0 + r_ * Ly::RAW, *rb = ra + Ly::RAW_A;
+      // ---- A: this thread's row, BK/2 complex values -> 8 TMEM columns of each plane
       {
-        float rh[8], rl[8], ih[8], il[8];
+        float rh[8], rl[8], ih[8], il[8];  // TF32: one value per column; BF16: packed pairs
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int c = 4 * a_kh + i;
-          const float4 v = *reinterpret_cast<const float4 *>(ra + a_row * 128 + ((c ^ (a_row & 7)) << 4));
-          split(v.x, rh[2 * i], rl[2 * i]);
-          split(v.y, ih[2 * i], il[2 * i]);
-          split(v.z, rh[2 * i + 1], rl[2 * i + 1]);
-          split(v.w, ih[2 * i + 1], il[2 * i + 1]);
+        for (int i = 0; i < BK / 4; ++i) {
+          const int c = a_kh * (BK / 4) + i;
+          const float4 v = *reinterpret_cast<const float4 *>(ra + a_row * Ly::RAW_A_ROW + ((c ^ (a_row & 7)) << 4));
+          float h0, l0, h1, l1, h2, l2, h3, l3;
+          if (BF) {
+            split_bf16(v.x, h0, l0);
+            split_bf16(v.y, h1, l1);
+            split_bf16(v.z, h2, l2);
+            split_bf16(v.w, h3, l3);
+            rh[i] = __uint_as_float(pack_bf16(h0, h2));
+            rl[i] = __uint_as_float(pack_bf16(l0, l2));
+            ih[i] = __uint_as_float(pack_bf16(h1, h3));
+            il[i] = __uint_as_float(pack_bf16(l1, l3));
+          } else {
+            split_tf32(v.x, rh[2 * i], rl[2 * i]);
+            split_tf32(v.y, ih[2 * i], il[2 * i]);
+            split_tf32(v.z, rh[2 * i + 1], rl[2 * i + 1]);
+            split_tf32(v.w, ih[2 * i + 1], il[2 * i + 1]);
+          }
         }
-        const uint32_t t = tmem + a_lane + D_COLS + (uint32_t)s * A_STAGE_COLS + 8u * a_kh;
+        const uint32_t t = tmem + a_lane + D_COLS + (uint32_t)s * Ly::A_STAGE_COLS + 8u * a_kh;
         tc::tmem_st8(t, rh);
-        tc::tmem_st8(t + BK, rl);
-        tc::tmem_st8(t + 2 * BK, ih);
-        tc::tmem_st8(t + 3 * BK, il);
+        tc::tmem_st8(t + 16, rl);
+        tc::tmem_st8(t + 32, ih);
+        tc::tmem_st8(t + 48, il);
       }
-      float4 rbv[4];
+      // ---- B: KG rows x two columns
+      float4 rbv[KG];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        rbv[j] = *reinterpret_cast<const float4 *>(rb + (4 * b_kq + j) * RAW_B_ROW + b_p * 16);
-      mbar_arrive(&raw_empty[r_]);  // this thread is done reading the raw tile
-      unsigned char *Bh = sm + s * STAGE, *Bl = Bh + B_PLANE;
-      // columns 2p and 2p+1; the column with parity b_kqlo goes first (bank spread)
+      for (int j = 0; j < KG; ++j)
+        rbv[j] = *reinterpret_cast<const float4 *>(rb + (KG * b_g + j) * Ly::RAW_B_ROW + b_p * 16);
+      tc::mbar_arrive_cta(&raw_empty[r_]);  // this thread is done reading the raw tile
+      unsigned char *Bh = sm + s * Ly::STAGE, *Bl = Bh + B_PLANE;
+      // columns 2p and 2p+1; the column with parity b_glo goes first (bank spread)
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const int cc = t ^ b_kqlo;
+        const int cc = t ^ b_glo;
         const int col = 2 * b_p + cc;
-        float4 rh, rl, ih, il;
-        const float x0 = cc ? rbv[0].z : rbv[0].x, x1 = cc ? rbv[1].z : rbv[1].x;
-        const float x2 = cc ? rbv[2].z : rbv[2].x, x3 = cc ? rbv[3].z : rbv[3].x;
-        const float y0 = cc ? rbv[0].w : rbv[0].y, y1 = cc ? rbv[1].w : rbv[1].y;
-        const float y2 = cc ? rbv[2].w : rbv[2].y, y3 = cc ? rbv[3].w : rbv[3].y;
-        split(x0, rh.x, rl.x);
-        split(x1, rh.y, rl.y);
-        split(x2, rh.z, rl.z);
-        split(x3, rh.w, rl.w);
-        split(y0, ih.x, il.x);
-        split(y1, ih.y, il.y);
-        split(y2, ih.z, il.z);
-        split(y3, ih.w, il.w);
-        const uint32_t o = tc::sw64_offset(col, 4 * b_kq);
-        const uint32_t ob = (uint32_t)BNC * 64u;  // one 128-row block
+        uint4 rh, rl, ih, il, nih, nil;
+        if (BF) {
+          float h[8], l[8], hi[8], li[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            split_bf16(cc ? rbv[j].z : rbv[j].x, h[j], l[j]);
+            split_bf16(cc ? rbv[j].w : rbv[j].y, hi[j], li[j]);
+          }
+          rh = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+          rl = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+          ih = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                          pack_bf16(hi[6], hi[7]));
+          il = make_uint4(pack_bf16(li[0], li[1]), pack_bf16(li[2], li[3]), pack_bf16(li[4], li[5]),
+                          pack_bf16(li[6], li[7]));
+          nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
+          nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
+        } else {
+          float h[4], l[4], hi[4], li[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            split_tf32(cc ? rbv[j].z : rbv[j].x, h[j], l[j]);
+            split_tf32(cc ? rbv[j].w : rbv[j].y, hi[j], li[j]);
+          }
+          rh = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+          rl = make_uint4(__float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]), __float_as_uint(l[3]));
+          ih = make_uint4(__float_as_uint(hi[0]), __float_as_uint(hi[1]), __float_as_uint(hi[2]),
+                          __float_as_uint(hi[3]));
+          il = make_uint4(__float_as_uint(li[0]), __float_as_uint(li[1]), __float_as_uint(li[2]),
+                          __float_as_uint(li[3]));
+          nih = make_uint4(ih.x ^ 0x80000000u, ih.y ^ 0x80000000u, ih.z ^ 0x80000000u, ih.w ^ 0x80000000u);
+          nil = make_uint4(il.x ^ 0x80000000u, il.y ^ 0x80000000u, il.z ^ 0x80000000u, il.w ^ 0x80000000u);
+        }
+        const uint32_t o = (uint32_t)col * 64u + ((uint32_t)(b_g ^ ((col >> 1) & 3)) << 4);
         // rows: [0,128) -Bi, [128,256) Br, [256,384) Bi
-        *reinterpret_cast<float4 *>(Bh + o) = make_float4(-ih.x, -ih.y, -ih.z, -ih.w);
-        *reinterpret_cast<float4 *>(Bh + ob + o) = rh;
-        *reinterpret_cast<float4 *>(Bh + 2 * ob + o) = ih;
-        *reinterpret_cast<float4 *>(Bl + o) = make_float4(-il.x, -il.y, -il.z, -il.w);
-        *reinterpret_cast<float4 *>(Bl + ob + o) = rl;
-        *reinterpret_cast<float4 *>(Bl + 2 * ob + o) = il;
+        *reinterpret_cast<uint4 *>(Bh + o) = nih;
+        *reinterpret_cast<uint4 *>(Bh + B_BLOCK + o) = rh;
+        *reinterpret_cast<uint4 *>(Bh + 2 * B_BLOCK + o) = ih;
+        *reinterpret_cast<uint4 *>(Bl + o) = nil;
+        *reinterpret_cast<uint4 *>(Bl + B_BLOCK + o) = rl;
+        *reinterpret_cast<uint4 *>(Bl + 2 * B_BLOCK + o) = il;
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async();
       tc::fence_before_sync();
-      mbar_arrive(&split_full[s]);
+      tc::mbar_arrive_cta(&split_full[s]);
     }
 
     // ---------------------------------------------------------------- epilogue
@@ -274,15 +358,22 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_tf32x3_kernel(int n, const flo
 
 }  // namespace
 
-size_t bse_tc_smem_bytes() { return (size_t)NSTAGE * STAGE + (size_t)NRAW * RAW + 1024; }
+size_t bse_tc_smem_bytes(int scheme) { return scheme == BF16X3 ? Layout<BF16X3>::SMEM : Layout<TF32X3>::SMEM; }
 
-cudaError_t launch_bse_tf32x3(cudaStream_t st, int n, int batch, const float2 *A, const float2 *B, float2 *Phi,
-                              float alpha, int *err) {
-  const size_t sm = bse_tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(bse_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_bse_split(cudaStream_t st, int scheme, int n, int batch, const float2 *A, const float2 *B,
+                             float2 *Phi, float alpha, int *err) {
+  const size_t sm = bse_tc_smem_bytes(scheme);
   dim3 grid((n + BNC - 1) / BNC, (n + BM - 1) / BM, batch);
-  bse_tf32x3_kernel<<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
+  cudaError_t e;
+  if (scheme == BF16X3) {
+    e = cudaFuncSetAttribute(bse_split_kernel<BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    bse_split_kernel<BF16X3><<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
+  } else {
+    e = cudaFuncSetAttribute(bse_split_kernel<TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    bse_split_kernel<TF32X3><<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
+  }
   return cudaGetLastError();
 }
 

@@ -86,9 +86,10 @@ cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64
 size_t assemble_smem_bytes(const Grid &g, bool c64);
 
 // split-precision BSE on the tensor cores (pq_gemm_tc.cu)
-size_t bse_tc_smem_bytes();
-cudaError_t launch_bse_tf32x3(cudaStream_t st, int n, int batch, const float2 *A, const float2 *B, float2 *Phi,
-                              float alpha, int *err);
+// scheme: 0 TF32x3, 1 BF16x3
+size_t bse_tc_smem_bytes(int scheme);
+cudaError_t launch_bse_split(cudaStream_t st, int scheme, int n, int batch, const float2 *A, const float2 *B,
+                             float2 *Phi, float alpha, int *err);
 
 // Sigma~2 (pq_sigma2.cu)
 cudaError_t launch_sigma2(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);

@@ -142,3 +142,28 @@ def test_split_tf32x3_iterations_match_oracle(name):
     print(name, errs)
     assert max(v for k, v in errs.items() if not k.startswith("phi")) < TOL_SPLIT, errs
     assert max(v for k, v in errs.items() if k.startswith("phi")) < 5 * TOL_SPLIT, errs
+
+
+@pytest.mark.parametrize("name", ["square_2x2_nu8_om8", "square_3x3_nu16_om8", "square_1x1_nu6_om5"])
+def test_split_bf16x3_iterations_match_oracle(name):
+    """BF16x3 split path against the FP64 oracle: BF16 hi/lo operands keep ~2^-16
+    per product, so Sigma, F and chi are checked within 5e-5, Phi within 3e-4."""
+    from paper_1510_03330_gb300.binding import Solver
+    from paper_1510_03330_gb300.workloads import SPLIT_BF16X3
+
+    p = CASES[name]
+    st = O.zero_state(p)
+    errs = {}
+    with Solver(p, precision=SPLIT_BF16X3) as s:
+        for it in range(3):
+            res = O.iterate(p, st)
+            st = res.state
+            s.iterate(1)
+            errs[f"sigma{it}"] = rel(s.sigma(), st.sigma)
+        errs["phi"] = rel(all_slices(s, s.Phi, p), st.phi)
+        errs["F"] = rel(all_slices(s, s.F, p), res.F)
+        chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
+        errs["chi_m"] = rel(s.chi(1), chi[1])
+    print(name, errs)
+    assert max(v for k, v in errs.items() if k != "phi") < 5e-5, errs
+    assert errs["phi"] < 3e-4, errs
