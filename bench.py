@@ -263,18 +263,19 @@ def main():
         compare = {"fp64_iter_per_s": 1.0 / fp64_s,
                    "fp64_bse_tflops": 8.0 * p.n**3 * 4 * p.n_Q / (fp64_bse_ms * 1e-3) / 1e12}
 
+    def relerr(x, y):
+        return float(np.abs(x - y).max() / np.abs(y).max())
+
+    def errors_vs_fp64(sol):
+        return {"iterations": 2, "sigma_rel_err": relerr(sol.sigma(), ref_sig),
+                "F_m_rel_err": relerr(sol.F(1, p.n_Q // 2), ref_F), "chi_m_rel_err": relerr(sol.chi(1), ref_chi)}
+
     solver = Solver(p, precision=a.precision, time_steps=True)
     if compare is not None:
         solver.iterate(2)
-
-        def relerr(x, y):
-            return float(np.abs(x - y).max() / np.abs(y).max())
-
-        compare.update({"iterations": 2, "sigma_rel_err": relerr(solver.sigma(), ref_sig),
-                        "F_m_rel_err": relerr(solver.F(1, p.n_Q // 2), ref_F),
-                        "chi_m_rel_err": relerr(solver.chi(1), ref_chi),
-                        "note": "max-norm errors relative to max|FP64| after two iterations from the zero state; "
-                                "F_m at Q = N_Q/2"})
+        compare.update(errors_vs_fp64(solver))
+        compare["note"] = ("max-norm errors relative to max|FP64| after two iterations from the zero state; "
+                           "F_m at Q = N_Q/2")
     for _ in range(a.warmup):
         solver.iterate(1)
     stream = torch.cuda.current_stream()
@@ -340,6 +341,30 @@ def main():
     if compare is not None:
         compare["split_over_fp64"] = value / compare["fp64_iter_per_s"]
         line["fp64_compare"] = compare
+        if a.precision == SPLIT_TF32X3:
+            # the faster, less precise split scheme on the same workload, for the same comparison
+            other = Solver(p, precision=SPLIT_BF16X3, time_steps=True)
+            other.iterate(2)
+            alt = errors_vs_fp64(other)
+            for _ in range(a.warmup):
+                other.iterate(1)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bse_ms = 0.0
+            f0.record(stream)
+            for _ in range(a.steps):
+                other.iterate(1)
+                bse_ms += other.step_times()["bse"]
+            f1.record(stream)
+            torch.cuda.synchronize()
+            alt_ms = f0.elapsed_time(f1)
+            other.close()
+            del other
+            torch.cuda.empty_cache()
+            alt.update({"iter_per_s": a.steps / (alt_ms / 1e3),
+                        "bse_tflops": bse_flops / (bse_ms / a.steps * 1e-3) / 1e12,
+                        "over_fp64": (a.steps / (alt_ms / 1e3)) / compare["fp64_iter_per_s"]})
+            line["split_bf16x3"] = alt
 
     if not a.no_e2e:
         # end to end through the public API: a fresh context (set-up, table uploads), K iterations

@@ -5,7 +5,7 @@
 // complex64, and the mixing Phi <- alpha C + (1 - alpha) Phi in the epilogue.
 // Each FP32 operand x is split into low-precision parts and a real product X Y
 // is taken over the leading part products, with FP32 accumulation:
-//   TF32x3: x = h + l (TF32), XY ~ Xh Yh + Xh Yl + Xl Yh          (~2^-22 per product)
+//   TF32x3: x = h + l (h TF32, l read as TF32), XY ~ Xh Yh + Xh Yl + Xl Yh   (~2^-22 per product)
 //   BF16x3: x = h + l (BF16), same three products                  (~2^-16 per product)
 //
 // Complex arithmetic as two real products into one 128 x 256 accumulator:
@@ -78,9 +78,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
                : "memory");
 }
 
+// h = tf32(x) exactly; the remainder is left in FP32 and the MMA uses its TF32 bits,
+// an error of at most 2^-11 |l| <= 2^-22 |x|
 __device__ __forceinline__ void split_tf32(float x, float &h, float &l) {
   h = tc::to_tf32(x);
-  l = tc::to_tf32(x - h);
+  l = x - h;
 }
 __device__ __forceinline__ void split_bf16(float x, float &h, float &l) {
   h = __bfloat162float(__float2bfloat16_rn(x));
@@ -198,24 +200,29 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
     unsigned char *raw0 = sm + NSTAGE * Ly::STAGE;
     constexpr int ACH = BK / 2;  // 16-byte chunks per raw A row
 
+    // With e = tid + NT * i a thread's chunks are one base plus constant strides:
+    // A row (tid / ACH) + i * (NT / ACH), chunk tid % ACH; B row (tid >> 6) + 4 i, chunk tid & 63.
+    const int fa_r = tid / ACH, fa_c = tid % ACH, fb_r = tid >> 6, fb_c = tid & 63;
+    const uint32_t fa_dst = (uint32_t)(fa_r * Ly::RAW_A_ROW + ((fa_c ^ (fa_r & 7)) << 4));
+    const uint32_t fb_dst = (uint32_t)(Ly::RAW_A + fb_r * Ly::RAW_B_ROW + fb_c * 16);
+    const float2 *fa_src = A + (long long)(row0 + fa_r) * n + 2 * fa_c;
+    const float2 *fb_src = B + (long long)fb_r * n + col0 + 2 * fb_c;
+    const uint32_t raw0_s = tc::smem_u32(raw0);
+    constexpr int A_RSTEP = NT / ACH;  // rows between a thread's A chunks
     auto fetch = [&](int kt) {
       const int r_ = kt % NRAW;
       if (kt >= NRAW) ok &= tc::mbar_wait(&raw_empty[r_], ((kt - NRAW) / NRAW) & 1, WAIT_TRIES);
-      unsigned char *ra = raw0 + r_ * Ly::RAW, *rb = ra + Ly::RAW_A;
+      const uint32_t base = raw0_s + (uint32_t)(r_ * Ly::RAW);
       const int k0 = kt * BK;
+      const bool ka = k0 + 2 * fa_c < n, cb = col0 + 2 * fb_c < n;
 #pragma unroll
       for (int i = 0; i < BK / 4; ++i) {
-        const int e = tid + NT * i;
-        const int r = e / ACH, c = e % ACH;  // A row, 16-byte chunk (2 complex values)
-        const int gr = row0 + r, k = k0 + 2 * c;
-        const bool va = gr < n && k < n;
-        cp_async16(tc::smem_u32(ra + r * Ly::RAW_A_ROW + ((c ^ (r & 7)) << 4)),
-                   va ? (const void *)(A + (long long)gr * n + k) : (const void *)A, va);
-        const int br = e >> 6, bc = e & 63;  // B row (k), 16-byte chunk (column pair)
-        const int gk = k0 + br, col = col0 + 2 * bc;
-        const bool vb = gk < n && col < n;
-        cp_async16(tc::smem_u32(rb + br * Ly::RAW_B_ROW + bc * 16),
-                   vb ? (const void *)(B + (long long)gk * n + col) : (const void *)B, vb);
+        const bool va = ka && row0 + fa_r + A_RSTEP * i < n;
+        cp_async16(base + fa_dst + (uint32_t)(i * A_RSTEP * Ly::RAW_A_ROW),
+                   va ? (const void *)(fa_src + (long long)A_RSTEP * i * n + k0) : (const void *)A, va);
+        const bool vb = cb && k0 + fb_r + 4 * i < n;
+        cp_async16(base + fb_dst + (uint32_t)(4 * i * Ly::RAW_B_ROW),
+                   vb ? (const void *)(fb_src + (long long)(k0 + 4 * i) * n) : (const void *)B, vb);
       }
       cp_async_mbar_arrive(&raw_full[r_]);
     };
