@@ -30,12 +30,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1510_03330_gb300.workloads import CONFIGS, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_TF32X3  # noqa: E402
+from paper_1510_03330_gb300.workloads import (CONFIGS, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_TF32X3,  # noqa: E402
+                                              batch_draw, device_bytes_bf16x3)
 
 METRIC = "parquet iter/s and BSE TFLOP/s: split-precision vs FP64 path at a stated Σ error"
 UNIT = "iter/s"
 DEFAULT_WORKLOAD = "square8_u2_b4"
-DEFAULT_PRECISION = SPLIT_TF32X3
+DEFAULT_PRECISION = SPLIT_BF16X3
+DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulate)",
+         SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
+# DRAM bytes of one launch / algorithmic bytes, from ncu captures on the 4x4 lattice
+# (profiles/bse_*_square4_u2_b5.md, profiles/assemble_*_square4_u2_b5.md)
+BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
+REMAP_TRAFFIC = {FP64: 1.112, SPLIT_TF32X3: 1.052}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
 LAUNCHES_PER_ITER = 18
@@ -187,13 +194,88 @@ def blas_threads():
 # ----------------------------------------------------------------------------- main
 
 
+BATCH = "batch64_seed1510"
+
+
+def pack_waves(draw, budget):
+    """First-fit decreasing packing of the solves into waves of at most budget device bytes."""
+    waves = []
+    for i in sorted(range(len(draw)), key=lambda i: -device_bytes_bf16x3(draw[i])):
+        b = device_bytes_bf16x3(draw[i])
+        for w in waves:
+            if w[1] + b <= budget:
+                w[0].append(i)
+                w[1] += b
+                break
+        else:
+            waves.append([[i], b])
+    return [sorted(w[0]) for w in waves]
+
+
+def run_batch(a, world, barrier, clk_factory):
+    """The 64 uneven solves: per memory wave, the solves iterated one at a time and then as one
+    batch (one graph per iteration, one grouped tensor-core launch); times summed over the waves."""
+    import torch
+
+    from paper_1510_03330_gb300.binding import Batch, Solver
+
+    draw = batch_draw(1510, 64)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    waves = pack_waves(draw, free - (8 << 30))
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    seq_ms = bat_ms = bse_ms = 0.0
+    tuned = []
+    clk = clk_factory()
+    clk.start()
+    for w in waves:
+        sols = [Solver(draw[i], precision=SPLIT_BF16X3, q_chunk=draw[i].n_k) for i in w]
+        for s_ in sols:
+            s_.iterate(1)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(a.steps):
+            for s_ in sols:
+                s_.iterate(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        b = Batch(sols, time_steps=True)
+        b.iterate(a.warmup + 4)  # the first iterations tune the grouped launch, then the graph is captured
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = ev(), ev()
+        f0.record(stream)
+        bse = 0.0
+        for _ in range(a.steps):
+            b.iterate(1)
+            bse += b.times()["bse"]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        bat_ms += f0.elapsed_time(f1)
+        bse_ms += bse
+        tuned.append(dict(b.config(), solves=len(w)))
+        b.close()
+        for s_ in sols:
+            s_.close()
+        del sols, b
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    flops = sum(8.0 * p.n**3 * 4 * p.n_Q for p in draw)
+    return {"waves": len(waves), "seq_ms": seq_ms, "batch_ms": bat_ms, "bse_ms": bse_ms, "tuned": tuned,
+            "flops_per_iter": flops, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(CONFIGS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(CONFIGS) + [BATCH])
     ap.add_argument("--precision", default=DEFAULT_PRECISION,
                     choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_BF16X6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -207,14 +289,30 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    p = CONFIGS[a.workload]
-    cfg = describe(a.workload, p, a.precision)
+    if a.workload == BATCH:
+        p = None
+        cfg = {"workload": "64 square-lattice Hubbard solves drawn with seed 1510 (numpy PCG64): L in 2..6, "
+                           "Nnu in {8,16,24,32}, NOmega = Nnu, U in [0.5, 3], beta in [2, 10], half filling",
+               "precision": SPLIT_BF16X3,
+               "l2": "inputs larger than L2 (vertex arrays of up to 171 GB per solve)"}
+    else:
+        p = CONFIGS[a.workload]
+        cfg = describe(a.workload, p, a.precision)
     cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
 
     if a.impl == "reference":
         if rank != 0:
             return 0
-        v, sample, secs = oracle_sample(p)
+        if p is None:
+            # the batch: the oracle on the smallest solve of the draw, scaled by the BSE flops of all 64
+            draw = batch_draw(1510, 64)
+            small = min(draw, key=lambda q: q.n**3 * q.n_Q)
+            v1, sample1, secs = oracle_sample(small)
+            scale = sum(q.n**3 * q.n_Q for q in draw) / (small.n**3 * small.n_Q)
+            v = v1 / scale
+            sample = f"{sample1}; smallest solve of the draw (L={small.L}, Nnu={small.n_nu}), x{scale:.0f} by BSE flops"
+        else:
+            v, sample, secs = oracle_sample(p)
         cores = blas_threads()
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
@@ -243,6 +341,34 @@ def main():
     def barrier():
         if dist:
             dist.barrier()
+
+    if a.workload == BATCH:
+        r = run_batch(a, world, barrier, lambda: ClockSampler(local))
+        ms = r["batch_ms"]
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        pk, src = peaks()
+        bse_tflops = r["flops_per_iter"] * a.steps / (r["bse_ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": bse_tflops, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": bse_tflops / pk["bf16_tflops"], "traffic": None, "kernel": "bse (grouped)",
+                "executed_tensor_frac": 3.0 * bse_tflops / pk["bf16_tflops"],
+                "peak_source": f"{src} bf16 burst"}
+        line = {"metric": METRIC, "value": world * a.steps / (ms / 1e3), "unit": "batch iter/s (64 solves)",
+                "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[SPLIT_BF16X3],
+                "data": "synthetic", "config": dict(cfg, waves=r["waves"]), "roofline": roof,
+                "one_at_a_time": {"value": a.steps / (r["seq_ms"] / 1e3), "unit": "batch iter/s (64 solves)",
+                                  "batched_over_one_at_a_time": r["seq_ms"] / r["batch_ms"]},
+                "tuned": r["tuned"], "bse_tflops": bse_tflops, "clocks": r["clocks"],
+                "gpu_launches": ((LAUNCHES_PER_ITER - 1) * 64 + 2) * a.steps,
+                "note": "per memory wave: solves iterated one at a time, then as one batch; times summed"}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     compare = None
     if a.precision != FP64 and not a.no_fp64_compare:
@@ -313,7 +439,9 @@ def main():
     steps = {k: v / a.steps for k, v in step_sum.items() if k != "total"}
     top = max(steps, key=steps.get)
     bse_flops = 8.0 * n**3 * 4 * nQ
-    remap_bytes = 12.0 * nQ * n * n * esz
+    # remap: read 4 Phi, write the BSE operands of 4 channels; BF16 planes are 8 bytes per
+    # complex for Gamma X and 12 for F (three pieces), otherwise one complex of esz each
+    remap_bytes = 4.0 * nQ * n * n * (esz + (20 if a.precision == SPLIT_BF16X3 else 2 * esz))
     bse_tflops = bse_flops / (steps["bse"] * 1e-3) / 1e12
     remap_gbs = remap_bytes / (steps["assemble"] * 1e-3) / 1e9
     if a.precision == FP64:
@@ -323,23 +451,25 @@ def main():
     else:
         ratio = {SPLIT_TF32X3: 1.1 / 2.25, SPLIT_BF16X3: 1.0, SPLIT_BF16X6: 1.0}[a.precision]
         peak = pk["bf16_tflops"] * ratio
-        # DRAM bytes per launch: the 4x4 ncu capture of this kernel moved 0.986 x the algorithmic
-        # 32 n^2 bytes per GEMM (read A, B, Phi; write Phi, complex64); scaled by n^2 x batch
+        # DRAM bytes per launch: ncu captures of each kernel on the 4x4 lattice, as a multiple of
+        # the algorithmic 32 n^2 bytes per GEMM (read A, B, Phi; write Phi), scaled by n^2 x batch
+        tr = BSE_TRAFFIC.get(a.precision)
         bse_roof = {"bound": "tensor", "achieved": bse_tflops, "peak": peak, "unit": "TFLOP/s",
-                    "frac": bse_tflops / peak, "traffic": 0.986 * 32.0 * n * n * 4 * nQ,
+                    "frac": bse_tflops / peak, "traffic": tr * 32.0 * n * n * 4 * nQ if tr else None,
                     "traffic_source": "ncu capture on the 4x4 lattice scaled by n^2 x batch",
+                    "executed_tensor_frac": 3.0 * bse_tflops / peak,
                     "peak_source": f"{src} bf16 burst x nominal ratio {ratio:.3f}"}
+    tr = REMAP_TRAFFIC.get(a.precision)
     remap_roof = {"bound": "hbm", "achieved": remap_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                  "frac": remap_gbs / pk["hbm_gbs"],
-                  "traffic": (1.052 * remap_bytes) if a.precision != FP64 else (1.112 * remap_bytes),
-                  "traffic_source": "ncu capture on the 4x4 lattice (1.05 x algorithmic c64, 1.11 x c128) scaled",
+                  "frac": remap_gbs / pk["hbm_gbs"], "traffic": tr * remap_bytes if tr else None,
+                  "traffic_source": "ncu capture on the 4x4 lattice, as a multiple of the algorithmic bytes, scaled",
                   "peak_source": f"{src} copy bandwidth"}
     roof = bse_roof if top == "bse" else (remap_roof if top == "assemble" else bse_roof)
     roof = dict(roof, kernel=top)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if a.precision == FP64 else "f32 (split operands, fp32 accumulate)",
+            "vs_baseline": None, "dtype": DTYPE[a.precision],
             "data": "synthetic", "config": cfg, "roofline": roof,
             "kernels": {"ms_per_iter": steps, "bse": bse_roof, "assemble": remap_roof},
             "bse_tflops": bse_tflops, "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
@@ -347,9 +477,10 @@ def main():
     if compare is not None:
         compare["split_over_fp64"] = value / compare["fp64_iter_per_s"]
         line["fp64_compare"] = compare
-        if a.precision == SPLIT_TF32X3:
-            # the faster, less precise split scheme on the same workload, for the same comparison
-            other = Solver(p, precision=SPLIT_BF16X3, time_steps=True)
+        if a.precision in (SPLIT_TF32X3, SPLIT_BF16X3):
+            # the other split scheme on the same workload, for the same comparison
+            alt_prec = SPLIT_TF32X3 if a.precision == SPLIT_BF16X3 else SPLIT_BF16X3
+            other = Solver(p, precision=alt_prec, time_steps=True)
             other.iterate(2)
             alt = errors_vs_fp64(other)
             for _ in range(a.warmup):
@@ -370,7 +501,7 @@ def main():
             alt.update({"iter_per_s": a.steps / (alt_ms / 1e3),
                         "bse_tflops": bse_flops / (bse_ms / a.steps * 1e-3) / 1e12,
                         "over_fp64": (a.steps / (alt_ms / 1e3)) / compare["fp64_iter_per_s"]})
-            line["split_bf16x3"] = alt
+            line[alt_prec] = alt
 
     if not a.no_e2e:
         # end to end through the public API: a fresh context (set-up, table uploads), K iterations

@@ -60,11 +60,15 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
 
 /* Arithmetic of the vertex storage and the BSE products.
  * PQ_FP64: complex128 vertices, FP64 everywhere.
- * PQ_SPLIT_*: complex64 vertices, parquet assembly in FP32; the BSE runs on the
+ * PQ_SPLIT_*: complex64 Phi, parquet assembly in FP32; the BSE runs on the
  * tensor cores as a split-operand product with FP32 accumulation; Dyson,
- * K1/K2 and the Sigma sums stay FP64.  PQ_SPLIT_TF32X3 (TF32 hi/lo,
- * ~2^-22 per product) and PQ_SPLIT_BF16X3 (BF16 hi/lo, ~2^-16, twice the K per
- * stage) are available; PQ_SPLIT_BF16X6 is rejected by pq_init with PQ_EINVAL. */
+ * K1/K2 and the Sigma sums stay FP64.
+ *   PQ_SPLIT_TF32X3: complex64 operands split into TF32 hi/lo inside the GEMM
+ *     (~2^-22 per product);
+ *   PQ_SPLIT_BF16X3: the assembly writes the operands as BF16 planes (hi/lo;
+ *     F also keeps a third piece), the GEMM reads them by TMA with no
+ *     conversion (~2^-16 per product, the fastest form);
+ *   PQ_SPLIT_BF16X6 is rejected by pq_init with PQ_EINVAL. */
 typedef enum {
   PQ_FP64 = 0,
   PQ_SPLIT_TF32X3 = 1,
@@ -81,6 +85,14 @@ typedef struct {
   int tau_order;          /* nodes per panel; default 16 */
   int tau_matsubara;      /* Matsubara cut M of G(tau): n in [-M, M-1]; default 2048 */
   int time_steps;         /* nonzero: record per-step CUDA-event times (pq_step_times) */
+  /* q-momenta whose transfer slices are assembled and multiplied per pass.
+   * 0 (default): all of them when the operand buffers of the whole box fit in
+   * free device memory, else the largest count that fits next to two copies
+   * of Phi.  With fewer than L*L per pass, Gamma and F are rebuilt pass by
+   * pass (the operand buffers hold 4*q_chunk*NOmega slices), Phi is double
+   * buffered for the Jacobi update, chi is computed during the iteration, and
+   * pq_get_F serves only the transfers of the last pass. */
+  int q_chunk;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */
@@ -182,6 +194,64 @@ PQ_API pq_status pq_sigma_second_order_noalloc(int lattice, double beta, double 
                                                int L, int n_nu, int n_omega, int tau_panels, int tau_order,
                                                int tau_matsubara, const double *sigma_dev, double *out_dev,
                                                void *cuda_stream);
+
+/* ---------------------------------------------------------------- batches
+ * A batch iterates several independent solves of uneven size together on one
+ * GPU.  Each iteration is one CUDA graph launch: every member's one-particle,
+ * kernel-function, self-energy and assembly steps, then ONE persistent grouped
+ * kernel over the tiles of all members' Bethe-Salpeter products, then a gather
+ * of every member's convergence scalars for a single device->host read.
+ * Members: contexts made by pq_init with PQ_SPLIT_BF16X3 and a single pass
+ * (q_chunk 0 or >= L*L, and the box fits), on one device and one cuda_stream,
+ * none poisoned.  The batch does not own them; they must outlive it, and
+ * pq_iterate on a member is refused while it exists (the other calls work
+ * between batch iterations).  The paper solves one problem at a time; this is
+ * a throughput layer over the same iteration. */
+typedef struct pq_batch pq_batch;
+
+typedef struct {
+  /* complex output columns per tile of the grouped kernel: 64 or 128; 0 = tune */
+  int tile_cols;
+  /* order of the members' tiles in the persistent schedule: 0 as given,
+   * 1 largest matrix first; -1 = tune */
+  int order;
+  /* nonzero: record the device time of the grouped kernel and of the whole
+   * iteration (pq_batch_times) */
+  int time_steps;
+} pq_batch_options;
+
+/* Fill *opt with the defaults: tune both choices, no timing. */
+PQ_API void pq_batch_default_options(pq_batch_options *opt);
+
+/* Group count contexts.  When a choice is left to tuning, the first
+ * iterations of pq_batch_iterate run the candidate grouped kernels in turn
+ * (each a full, real iteration: the candidates compute the same products) and
+ * keep the fastest; the graph is captured after that.  Errors: PQ_EINVAL (a
+ * member that does not qualify, count < 1), PQ_ENOMEM, PQ_ECUDA;
+ * pq_last_error(NULL) gives the message. */
+PQ_API pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const pq_batch_options *opt);
+
+/* Run n_iter iterations of every member.  max_dsigma, when non-NULL, receives
+ * count values: each member's max_k |Sigma_new - Sigma| of the last
+ * iteration.  A member's PQ_ENAN or a timed-out device wait (PQ_ETIMEOUT)
+ * poisons the batch and the members concerned. */
+PQ_API pq_status pq_batch_iterate(pq_batch *b, int n_iter, double *max_dsigma);
+
+/* The grouped kernel's configuration: tile columns, order (as in
+ * pq_batch_options; -1 while tuning is not finished) and, when tuned, the
+ * device time in ms of each candidate (tile_cols 128/64 x order 0/1, in that
+ * order; 0 where not run) in tuned_ms[4]. */
+PQ_API pq_status pq_batch_config(const pq_batch *b, int *tile_cols, int *order, float *tuned_ms);
+
+/* Device times (ms) of the last iteration when time_steps was set: out[0] =
+ * the whole iteration (graph launch), out[1] = the grouped BSE kernel. */
+PQ_API pq_status pq_batch_times(const pq_batch *b, float *out2);
+
+/* Message of the last failure on the batch. */
+PQ_API const char *pq_batch_last_error(const pq_batch *b);
+
+/* Release the batch (the members stay valid and can be iterated alone).  NULL is a no-op. */
+PQ_API void pq_batch_destroy(pq_batch *b);
 
 /* Message of the last failure on ctx (or, when ctx is NULL, of the last
  * failed call that has no context: pq_init or pq_sigma_second_order_noalloc). */

@@ -38,11 +38,16 @@ class Options(C.Structure):
         ("tau_order", C.c_int),
         ("tau_matsubara", C.c_int),
         ("time_steps", C.c_int),
+        ("q_chunk", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
     ]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("tile_cols", C.c_int), ("order", C.c_int), ("time_steps", C.c_int)]
 
 
 class ParquetError(RuntimeError):
@@ -98,6 +103,20 @@ def load_library(path: str = LIB_PATH):
     lib.pq_last_error.restype = C.c_char_p
     lib.pq_destroy.argtypes = [P]
     lib.pq_destroy.restype = None
+    lib.pq_batch_default_options.argtypes = [C.POINTER(BatchOptions)]
+    lib.pq_batch_default_options.restype = None
+    lib.pq_batch_create.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int, C.POINTER(BatchOptions)]
+    lib.pq_batch_create.restype = C.c_int
+    lib.pq_batch_iterate.argtypes = [P, C.c_int, D]
+    lib.pq_batch_iterate.restype = C.c_int
+    lib.pq_batch_config.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    lib.pq_batch_config.restype = C.c_int
+    lib.pq_batch_times.argtypes = [P, C.POINTER(C.c_float)]
+    lib.pq_batch_times.restype = C.c_int
+    lib.pq_batch_last_error.argtypes = [P]
+    lib.pq_batch_last_error.restype = C.c_char_p
+    lib.pq_batch_destroy.argtypes = [P]
+    lib.pq_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -138,7 +157,8 @@ class _TorchAllocator:
 class Solver:
     """One parquet solve on the GPU (C ABI: pq_init ... pq_destroy)."""
 
-    def __init__(self, p: Params, precision: str = FP64, time_steps: bool = False, use_torch: bool = True):
+    def __init__(self, p: Params, precision: str = FP64, time_steps: bool = False, use_torch: bool = True,
+                 q_chunk: int = 0):
         lib = load_library()
         self.p = p
         self.lib = lib
@@ -151,6 +171,7 @@ class Solver:
         o.tau_order = p.tau_order
         o.tau_matsubara = p.tau_matsubara
         o.time_steps = 1 if time_steps else 0
+        o.q_chunk = q_chunk
         self._alloc = None
         if use_torch:
             import torch
@@ -257,3 +278,58 @@ class Solver:
     @property
     def device_bytes(self) -> int:
         return int(self.sizes[6])
+
+
+class Batch:
+    """Several solves iterated together (C ABI: pq_batch_create ... pq_batch_destroy): per iteration
+    one CUDA graph with one grouped tensor-core launch for all the Bethe-Salpeter products."""
+
+    def __init__(self, solvers, tile_cols: int = 0, order: int = -1, time_steps: bool = False):
+        lib = load_library()
+        self.lib = lib
+        self.solvers = list(solvers)
+        o = BatchOptions()
+        lib.pq_batch_default_options(C.byref(o))
+        o.tile_cols, o.order, o.time_steps = tile_cols, order, 1 if time_steps else 0
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        h = C.c_void_p()
+        st = lib.pq_batch_create(C.byref(h), arr, len(self.solvers), C.byref(o))
+        if st != PQ_OK:
+            raise ParquetError(st, lib.pq_last_error(None).decode())
+        self.h = h
+
+    def iterate(self, n_iter: int = 1) -> np.ndarray:
+        """Run n_iter iterations of every member; returns each member's last max|dSigma|."""
+        out = np.zeros(len(self.solvers))
+        st = self.lib.pq_batch_iterate(self.h, n_iter, _dptr(out))
+        if st != PQ_OK:
+            raise ParquetError(st, self.lib.pq_batch_last_error(self.h).decode())
+        return out
+
+    def config(self):
+        tc, od = C.c_int(0), C.c_int(0)
+        tuned = (C.c_float * 4)()
+        self.lib.pq_batch_config(self.h, C.byref(tc), C.byref(od), tuned)
+        return {"tile_cols": tc.value, "order": od.value, "tuned_ms": [float(x) for x in tuned]}
+
+    def times(self):
+        out = (C.c_float * 2)()
+        self.lib.pq_batch_times(self.h, out)
+        return {"iteration": float(out[0]), "bse": float(out[1])}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

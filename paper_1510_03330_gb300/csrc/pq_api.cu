@@ -11,30 +11,11 @@
 #include <string>
 #include <vector>
 
-#include "../../include/parquet.h"
-#include "pq_common.cuh"
-#include "pq_internal.h"
+#include "pq_ctx.h"
 
 using pq::Buffers;
 using pq::Grid;
 using pq::Sizes;
-
-struct pq_ctx {
-  Grid g{};
-  Sizes z{};
-  pq_options opt{};
-  Buffers b{};
-  cudaStream_t st = nullptr;
-  bool c64 = false;
-  bool poisoned = false;
-  double lam[8] = {0};
-  std::vector<std::pair<void *, size_t>> allocs;
-  size_t bytes = 0;
-  std::string err;
-  cudaEvent_t ev[PQ_NSTEPS + 1] = {};
-  float times[PQ_NSTEPS] = {0};
-  int iterations = 0;
-};
 
 namespace {
 
@@ -43,7 +24,9 @@ std::string g_init_err;
 const char *kStepNames[PQ_NSTEPS] = {"dyson",    "bubbles",      "kernels", "sigma1", "sigma2",
                                      "assemble", "sigma_update", "bse",     "total"};
 
-pq_status fail(pq_ctx *c, pq_status s, const char *fmt, ...) {
+}  // namespace
+
+pq_status pq::fail(pq_ctx *c, pq_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -57,6 +40,9 @@ pq_status fail(pq_ctx *c, pq_status s, const char *fmt, ...) {
   }
   return s;
 }
+
+namespace {
+using pq::fail;
 
 #define CK(call)                                                                              \
   do {                                                                                        \
@@ -124,16 +110,31 @@ size_t vbytes(const pq_ctx *c) {
   return (size_t)4 * c->g.nQ * (size_t)c->g.n * c->g.n * (c->c64 ? sizeof(float2) : sizeof(double2));
 }
 
+// Bytes per complex element of the BSE operands (gam, fv) in each storage format.
+size_t gam_es(int vfmt) { return vfmt == pq::V_C128 ? 16 : 8; }
+size_t fv_es(int vfmt) { return vfmt == pq::V_C128 ? 16 : vfmt == pq::V_C64 ? 8 : 12; }
+
+int num_passes(const pq_ctx *c) { return (c->g.nk + c->b.q_chunk - 1) / c->b.q_chunk; }
+
+size_t b_fv_bytes(const pq_ctx *c) {
+  return (size_t)c->b.q_chunk * 4 * c->g.n_om * (size_t)c->g.n * c->b.ld * fv_es(c->b.vfmt);
+}
+
 __global__ void phi_from_c128(float2 *dst, const double2 *src, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) dst[i] = make_float2((float)src[i].x, (float)src[i].y);
 }
 
-pq_status run_iteration(pq_ctx *c, double *dmax) {
+// Device work of one iteration, queued on the context's stream without waiting.  With
+// bse == false the products of a single-pass iteration are left out (a batch runs them in
+// its grouped launch); timing records the step events.
+}  // namespace
+
+pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
   cudaStream_t st = c->st;
   Grid &g = c->g;
   Buffers &b = c->b;
-  const bool tm = c->opt.time_steps != 0;
+  const bool tm = timing;
   auto mark = [&](int i) {
     if (tm) cudaEventRecord(c->ev[i], st);
   };
@@ -148,38 +149,114 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
   mark(4);
   CK(pq::launch_sigma2(st, g, c->z, b));
   mark(5);
-  CK(pq::launch_assemble(st, g, b, c->c64, c->lam));
-  mark(6);
-  CK(pq::launch_sigma_update(st, g, b));
-  mark(7);
   const long long nn = g.n;
-  if (!c->c64) {
-    CK(pq::zgemm_fp64(st, g.n, g.n, g.n, make_double2(g.mix, 0.0), (const double2 *)b.gam, g.n, nn * nn,
-                      (const double2 *)b.fv, g.n, nn * nn, make_double2(1.0 - g.mix, 0.0), (double2 *)b.phi, g.n,
-                      nn * nn, 4 * g.nQ));
-  } else {
-    CK(pq::launch_bse_split(st, c->opt.precision == PQ_SPLIT_BF16X3 ? 1 : 0, g.n, 4 * g.nQ,
-                            (const float2 *)b.gam, (const float2 *)b.fv, (float2 *)b.phi, (float)g.mix,
-                            (int *)(b.scal + 4)));
+  const int np = num_passes(c);
+  const bool fused = (np == 1);
+  c->chi_ready = false;
+  for (int ip = 0; ip < np; ++ip) {
+    pq::Pass p;
+    p.qb = ip * b.q_chunk;
+    p.nq = std::min(b.q_chunk, g.nk - p.qb);
+    p.fused = fused;
+    p.accumulate = ip > 0;
+    const int zc = p.nq * g.n_om;
+    const long long q0 = (long long)p.qb * g.n_om;
+    if (tm && !fused) cudaEventRecord(c->pev[3 * ip], st);
+    CK(pq::launch_assemble(st, g, b, c->lam, p));
+    if (!fused) CK(pq::launch_chi(st, g, b, p.qb, p.nq));
+    if (fused) {
+      mark(6);
+      CK(pq::launch_sigma_update(st, g, b));
+      mark(7);
+    } else if (tm) {
+      cudaEventRecord(c->pev[3 * ip + 1], st);
+    }
+    void *phi_out = fused ? b.phi : b.phi_new;
+    if (!bse) {
+      // left to the caller
+    } else if (b.vfmt == pq::V_BF16P) {
+      const pq::BseProblem *pr = c->probs + (fused ? 0 : (c->swapped ? np : 0) + ip);
+      CK(pq::launch_bse_tma(st, 128, pr, 1, pq::bse_tiles(128, g.n, 4 * zc), (int *)(b.scal + 4), 0));
+    } else {
+      // in-place products: a separate Jacobi target first receives the old slices
+      const size_t es = b.vfmt == pq::V_C128 ? sizeof(double2) : sizeof(float2);
+      const int nr = fused ? 1 : 4;  // one launch over all channels, or one per channel slice range
+      for (int r = 0; r < nr; ++r) {
+        const size_t po = ((size_t)r * g.nQ + q0) * nn * nn * es, oo = (size_t)r * zc * nn * nn * es;
+        char *dst = (char *)phi_out + po;
+        if (!fused) CK(cudaMemcpyAsync(dst, (const char *)b.phi + po, (size_t)zc * nn * nn * es,
+                                       cudaMemcpyDeviceToDevice, st));
+        const int batch = fused ? 4 * zc : zc;
+        if (b.vfmt == pq::V_C128) {
+          CK(pq::zgemm_fp64(st, g.n, g.n, g.n, make_double2(g.mix, 0.0), (const double2 *)((char *)b.gam + oo), g.n,
+                            nn * nn, (const double2 *)((char *)b.fv + oo), g.n, nn * nn,
+                            make_double2(1.0 - g.mix, 0.0), (double2 *)dst, g.n, nn * nn, batch));
+        } else {
+          CK(pq::launch_bse_split(st, g.n, batch, (const float2 *)((char *)b.gam + oo),
+                                  (const float2 *)((char *)b.fv + oo), (float2 *)dst, (float)g.mix,
+                                  (int *)(b.scal + 4)));
+        }
+      }
+    }
+    if (tm && !fused) cudaEventRecord(c->pev[3 * ip + 2], st);
+    c->last_qb = p.qb;
+  }
+  if (!fused) {
+    mark(6);
+    CK(pq::launch_sigma_update(st, g, b));
+    mark(7);
+    std::swap(b.phi, b.phi_new);
+    c->swapped = !c->swapped;
+    c->chi_ready = true;
   }
   mark(8);
-  double h[5];
-  CK(cudaMemcpyAsync(h, b.scal, sizeof h, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  return PQ_OK;
+}
+
+// Host side of the end of an iteration: h = the first five scalars of the context
+// (max |dSigma|, non-finite flag, tensor-core timeout flag) read after the work completed.
+pq_status pq::finish_iteration(pq_ctx *c, const double *h, double *dmax, bool timing) {
+  const int np = num_passes(c);
+  const bool fused = (np == 1);
   int timeout_flag;
   std::memcpy(&timeout_flag, &h[4], sizeof timeout_flag);
   if (timeout_flag) {
     c->poisoned = true;
     return fail(c, PQ_ETIMEOUT, "a tensor-core pipeline wait gave up; the state is invalid");
   }
-  if (tm) {
+  if (timing) {
     for (int i = 0; i < PQ_NSTEPS - 1; ++i) cudaEventElapsedTime(&c->times[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&c->times[PQ_NSTEPS - 1], c->ev[0], c->ev[PQ_NSTEPS - 1]);
+    if (!fused) {
+      // the passes interleave assembly and products: sum each over the passes
+      float t_asm = 0.f, t_bse = 0.f;
+      for (int ip = 0; ip < np; ++ip) {
+        float a = 0.f, m = 0.f;
+        cudaEventElapsedTime(&a, c->pev[3 * ip], c->pev[3 * ip + 1]);
+        cudaEventElapsedTime(&m, c->pev[3 * ip + 1], c->pev[3 * ip + 2]);
+        t_asm += a;
+        t_bse += m;
+      }
+      c->times[5] = t_asm;  // assemble (with chi)
+      c->times[7] = t_bse;  // bse
+    }
   }
   if (h[2] != 0.0 || !std::isfinite(h[1])) return fail(c, PQ_ENAN, "non-finite self-energy after iteration");
   *dmax = h[1];
   c->iterations++;
   return PQ_OK;
+}
+
+namespace {
+
+pq_status run_iteration(pq_ctx *c, double *dmax) {
+  const bool tm = c->opt.time_steps != 0;
+  pq_status s = pq::enqueue_iteration(c, true, tm);
+  if (s != PQ_OK) return s;
+  double h[5];
+  CK(cudaMemcpyAsync(h, c->b.scal, sizeof h, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return pq::finish_iteration(c, h, dmax, tm);
 }
 
 }  // namespace
@@ -272,23 +349,53 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   c->lam[4] = 2.0 * U;
   c->lam[6] = 0.0;
 
+  Buffers &b = c->b;
+  b.vfmt = o.precision == PQ_FP64 ? pq::V_C128 : o.precision == PQ_SPLIT_TF32X3 ? pq::V_C64 : pq::V_BF16P;
+  b.ld = b.vfmt == pq::V_BF16P ? (g.n + 7) / 8 * 8 : g.n;  // TMA rows: multiples of 16 bytes
+  if (o.q_chunk < 0) {
+    delete c;
+    return fail(nullptr, PQ_EINVAL, "q_chunk must be >= 0");
+  }
+
   if (pq::assemble_smem_bytes(g, c->c64) > 200 * 1024) {
     delete c;
     return fail(nullptr, PQ_EINVAL, "NOmega*Nnu = %d too large for one vertex block in shared memory",
                 n_Omega * n_nu);
   }
 
-  // device memory
+  // device memory: the state Phi, and the operand buffers of q_chunk q-momenta per pass; with
+  // fewer than all momenta per pass the Jacobi update needs a second Phi
   const size_t vb = vbytes(c);
   const size_t cs = sizeof(double2);
-  Buffers &b = c->b;
+  const size_t per_q = (size_t)4 * g.n_om * (size_t)g.n * b.ld * (gam_es(b.vfmt) + fv_es(b.vfmt));
+  if (o.q_chunk > 0) {
+    b.q_chunk = std::min(o.q_chunk, g.nk);
+  } else {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    const size_t small = (size_t)64 << 20, margin = (size_t)2 << 30;  // tables, and room for the caller
+    const size_t avail = fr > margin ? fr - margin : 0;
+    if (fr == 0 || vb + per_q * g.nk + small <= avail) {
+      b.q_chunk = g.nk;
+    } else {
+      const size_t left = avail > 2 * vb + small ? avail - 2 * vb - small : 0;
+      b.q_chunk = (int)std::max<size_t>(1, std::min<size_t>(g.nk, left / per_q));
+    }
+  }
+  const bool several = b.q_chunk < g.nk;
+  const size_t obytes_g = (size_t)b.q_chunk * 4 * g.n_om * (size_t)g.n * b.ld * gam_es(b.vfmt);
+  const size_t obytes_f = (size_t)b.q_chunk * 4 * g.n_om * (size_t)g.n * b.ld * fv_es(b.vfmt);
   struct Req {
     void **p;
     size_t bytes;
   } reqs[] = {
       {&b.phi, vb},
-      {&b.gam, vb},
-      {&b.fv, vb},
+      {&b.phi_new, several ? vb : 0},
+      {&b.gam, obytes_g},
+      {&b.fv, obytes_f},
       {(void **)&b.sigma, cs * g.nk * g.n_ext},
       {(void **)&b.sigma_new, cs * g.nk * g.n_ext},
       {(void **)&b.sigma1, cs * g.nk * g.n_ext},
@@ -321,6 +428,7 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   size_t need = 0;
   for (auto &r : reqs) need += (r.bytes + 255) & ~(size_t)255;
   for (auto &r : reqs) {
+    if (r.bytes == 0) continue;
     *r.p = dalloc(c, r.bytes);
     if (!*r.p) {
       release_all(c);
@@ -374,6 +482,43 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   }
   for (int i = 0; s == PQ_OK && i <= PQ_NSTEPS; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) s = fail(c, PQ_ECUDA, "event create failed");
+  if (s == PQ_OK && several && o.time_steps) {
+    c->pev.assign(3 * (size_t)num_passes(c), nullptr);
+    for (auto &e : c->pev)
+      if (s == PQ_OK && cudaEventCreate(&e) != cudaSuccess) s = fail(c, PQ_ECUDA, "event create failed");
+  }
+  if (s == PQ_OK && b.vfmt == pq::V_BF16P) {
+    // problem table of the TMA-fed BSE: per pass, and per assignment of the Phi buffers
+    CUtensorMap mA, mB;
+    CUresult r = pq::make_bse_maps(b.gam, b.fv, g.n, b.ld, 4LL * b.q_chunk * g.n_om, &mA, &mB);
+    if (r != CUDA_SUCCESS) s = fail(c, PQ_ECUDA, "tensor map encoding failed (CUresult %d)", (int)r);
+    const int np = num_passes(c);
+    std::vector<pq::BseProblem> tab(several ? 2 * np : 1);
+    for (size_t i = 0; i < tab.size(); ++i) {
+      const int ip = (int)(i % np), sw = (int)(i / np);
+      const int nq = std::min(b.q_chunk, g.nk - ip * b.q_chunk);
+      pq::BseProblem &e = tab[i];
+      e.mapA = mA;
+      e.mapB = mB;
+      e.tile0 = 0;
+      e.n = g.n;
+      e.zc = nq * g.n_om;
+      e.batch = 4 * e.zc;
+      e.pad_ = 0;
+      e.phi_cs = g.nQ;
+      e.phi_q0 = (long long)ip * b.q_chunk * g.n_om;
+      void *cur = sw ? b.phi_new : b.phi, *nxt = several ? (sw ? b.phi : b.phi_new) : b.phi;
+      e.phi_in = (const float2 *)cur;
+      e.phi_out = (float2 *)nxt;
+      e.alpha = (float)g.mix;
+    }
+    c->prob_host = tab[0];
+    if (s == PQ_OK) {
+      c->probs = (pq::BseProblem *)dalloc(c, tab.size() * sizeof(pq::BseProblem));
+      if (!c->probs) s = fail(c, PQ_ENOMEM, "device allocation of the BSE problem table failed");
+    }
+    up(c->probs, tab.data(), tab.size() * sizeof(pq::BseProblem));
+  }
   if (s != PQ_OK) {
     g_init_err = c->err;
     pq_destroy(c);
@@ -395,6 +540,7 @@ pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, doubl
   if (!c) return PQ_EINVAL;
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned by an earlier error: %s", c->err.c_str());
   if (max_iter < 0) return fail(c, PQ_EINVAL, "max_iter < 0");
+  if (c->in_batch) return fail(c, PQ_EINVAL, "the context belongs to a batch: iterate it with pq_batch_iterate");
   double d = INFINITY;
   int it = 0;
   for (; it < max_iter; ++it) {
@@ -424,7 +570,7 @@ pq_status pq_get_Sigma(const pq_ctx *cc, double *out, size_t len) {
   return PQ_OK;
 }
 
-static pq_status get_matrix(pq_ctx *c, const void *base, int channel, int Q, double *out, size_t len) {
+static pq_status get_phi_matrix(pq_ctx *c, int channel, int Q, double *out, size_t len) {
   if (!out || channel < 0 || channel > 3 || Q < 0 || Q >= c->g.nQ)
     return fail(c, PQ_EINVAL, "bad channel %d or Q %d", channel, Q);
   const size_t nn = (size_t)c->g.n * c->g.n;
@@ -432,10 +578,10 @@ static pq_status get_matrix(pq_ctx *c, const void *base, int channel, int Q, dou
   CK(cudaStreamSynchronize(c->st));
   const size_t off = ((size_t)channel * c->g.nQ + Q) * nn;
   if (!c->c64) {
-    CK(cudaMemcpy(out, (const double2 *)base + off, nn * sizeof(double2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out, (const double2 *)c->b.phi + off, nn * sizeof(double2), cudaMemcpyDeviceToHost));
   } else {
     std::vector<float2> tmp(nn);
-    CK(cudaMemcpy(tmp.data(), (const float2 *)base + off, nn * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tmp.data(), (const float2 *)c->b.phi + off, nn * sizeof(float2), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < nn; ++i) {
       out[2 * i] = tmp[i].x;
       out[2 * i + 1] = tmp[i].y;
@@ -449,14 +595,61 @@ pq_status pq_get_F(const pq_ctx *cc, int channel, int Q, double *out, size_t len
   if (!c) return PQ_EINVAL;
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
   if (c->iterations == 0) return fail(c, PQ_EINVAL, "no iteration has run yet");
-  return get_matrix(c, c->b.fv, channel, Q, out, len);
+  const Grid &g = c->g;
+  const pq::Buffers &b = c->b;
+  if (!out || channel < 0 || channel > 3 || Q < 0 || Q >= g.nQ)
+    return fail(c, PQ_EINVAL, "bad channel %d or Q %d", channel, Q);
+  const int nq = std::min(b.q_chunk, g.nk - c->last_qb);
+  const int Ql = Q - c->last_qb * g.n_om;
+  if (Ql < 0 || Ql >= nq * g.n_om)
+    return fail(c, PQ_EINVAL, "F of Q %d is not kept: the last pass held q-momenta %d..%d", Q, c->last_qb,
+                c->last_qb + nq - 1);
+  const size_t n = g.n, ld = b.ld, nn = n * n;
+  if (len < 2 * nn) return fail(c, PQ_EINVAL, "matrix needs %zu doubles, got %zu", 2 * nn, len);
+  CK(cudaStreamSynchronize(c->st));
+  const size_t slab = (size_t)channel * nq * g.n_om + Ql;
+  if (b.vfmt == pq::V_C128) {
+    CK(cudaMemcpy(out, (const double2 *)b.fv + slab * nn, nn * sizeof(double2), cudaMemcpyDeviceToHost));
+  } else if (b.vfmt == pq::V_C64) {
+    std::vector<float2> tmp(nn);
+    CK(cudaMemcpy(tmp.data(), (const float2 *)b.fv + slab * nn, nn * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < nn; ++i) {
+      out[2 * i] = tmp[i].x;
+      out[2 * i + 1] = tmp[i].y;
+    }
+  } else {
+    // six BF16 planes (Re h, Im h, Re l, Im l, Re r, Im r); element value = h + l + r
+    const size_t ps = (size_t)4 * b.q_chunk * g.n_om * n * ld;  // plane stride of the buffer
+    std::vector<uint16_t> tmp(6 * n * ld);
+    for (int w = 0; w < 6; ++w)
+      CK(cudaMemcpy(tmp.data() + w * n * ld, (const uint16_t *)b.fv + w * ps + slab * n * ld, n * ld * 2,
+                    cudaMemcpyDeviceToHost));
+    auto bf = [](uint16_t h) {
+      uint32_t u = (uint32_t)h << 16;
+      float f;
+      std::memcpy(&f, &u, 4);
+      return (double)f;
+    };
+    for (size_t i = 0; i < n; ++i)
+      for (size_t j = 0; j < n; ++j) {
+        const size_t e = i * ld + j;
+        double re = 0.0, im = 0.0;
+        for (int piece = 0; piece < 3; ++piece) {
+          re += bf(tmp[(2 * piece) * n * ld + e]);
+          im += bf(tmp[(2 * piece + 1) * n * ld + e]);
+        }
+        out[2 * (i * n + j)] = re;
+        out[2 * (i * n + j) + 1] = im;
+      }
+  }
+  return PQ_OK;
 }
 
 pq_status pq_get_Phi(const pq_ctx *cc, int channel, int Q, double *out, size_t len) {
   pq_ctx *c = const_cast<pq_ctx *>(cc);
   if (!c) return PQ_EINVAL;
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
-  return get_matrix(c, c->b.phi, channel, Q, out, len);
+  return get_phi_matrix(c, channel, Q, out, len);
 }
 
 pq_status pq_get_chi(const pq_ctx *cc, int channel, double *out, size_t len) {
@@ -466,7 +659,7 @@ pq_status pq_get_chi(const pq_ctx *cc, int channel, double *out, size_t len) {
   if (channel < 0 || channel > 3) return fail(c, PQ_EINVAL, "bad channel %d", channel);
   if (c->iterations == 0) return fail(c, PQ_EINVAL, "no iteration has run yet");
   if (len < (size_t)2 * c->g.nQ) return fail(c, PQ_EINVAL, "chi needs %d doubles", 2 * c->g.nQ);
-  CK(pq::launch_chi(c->st, c->g, c->b, c->c64));
+  if (!c->chi_ready) CK(pq::launch_chi(c->st, c->g, c->b, 0, c->g.nk));
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(out, c->b.chi + (size_t)channel * c->g.nQ, sizeof(double2) * c->g.nQ, cudaMemcpyDeviceToHost));
   return PQ_OK;
@@ -503,7 +696,8 @@ pq_status pq_set_state(pq_ctx *c, const double *phi, const double *sigma) {
       CK(cudaMemcpy(c->b.phi, phi, ne * sizeof(double2), cudaMemcpyHostToDevice));
     } else {
       // stage through the F buffer, which the next iteration overwrites
-      const long long chunk = vbytes(c) / sizeof(double2);
+      const long long chunk =
+          (long long)b_fv_bytes(c) / (long long)sizeof(double2);
       for (long long o = 0; o < ne; o += chunk) {
         long long cnt = std::min(chunk, ne - o);
         CK(cudaMemcpy(c->b.fv, phi + 2 * o, cnt * sizeof(double2), cudaMemcpyHostToDevice));
@@ -545,6 +739,8 @@ void pq_destroy(pq_ctx *c) {
   cudaStreamSynchronize(c->st);
   for (int i = 0; i <= PQ_NSTEPS; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (auto e : c->pev)
+    if (e) cudaEventDestroy(e);
   release_all(c);
   delete c;
 }

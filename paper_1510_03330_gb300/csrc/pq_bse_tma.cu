@@ -1,0 +1,359 @@
+// BF16x3 Bethe-Salpeter products fed by TMA from pre-split operand planes.
+//
+// For every (r, Q) the BSE (App. A, Eq. PA_F_Phi) is one complex n x n x n
+// product C = A B with A = s_r Gamma_r(Q) diag(X_r(Q)) and B = F_r(Q), and the
+// mixing Phi <- alpha C + (1 - alpha) Phi in the epilogue.  The parquet
+// assembly writes both operands already split into BF16 planes
+// (x = h + l with h = bf16(x), l = bf16(x - h); F also keeps a third piece for
+// readback), so this kernel does no conversion at all: a real product XY is
+// taken as Xh Yh + Xh Yl + Xl Yh on the tensor cores with FP32 accumulation.
+//
+// Complex arithmetic per split product, into one 128 x 256 FP32 accumulator
+// (Re C in columns 0..127, Im C in 128..255):
+//   D[0:256]   += Ar [Br | Bi]     (N = 256: the Br and Bi planes sit side by side)
+//   D[0:128]   += (-Ai) Bi         (N = 128, negated A)
+//   D[128:256] += Ai Br            (N = 128)
+//
+// Operand layouts in shared memory (written by TMA, read by the MMAs):
+//   A plane: 128 rows x 32 k, K-major, 64-byte rows with the 64-byte swizzle;
+//   B plane: 32 k x 128 columns, MN-major, two 64-column atoms of 32 rows x 128 B
+//            with the 128-byte swizzle; the planes of one stage are ordered
+//            Brh, Bih, Brl, Bil so that [Br | Bi] is one N = 256 operand.
+//
+// Persistent kernel, one CTA per SM, warp-specialised: warp 0 issues the TMA
+// loads of a 3-stage ring, warp 1 issues the MMAs, warps 2..9 run the epilogue.
+// Tensor memory holds two accumulators, so the epilogue of one tile overlaps
+// the main loop of the next.  Every mbarrier wait is bounded in time; a wait
+// that gives up sets the error flag and the CTA winds down (draining its
+// in-flight copies and MMAs, then freeing tensor memory).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "pq_common.cuh"
+#include "pq_internal.h"
+#include "pq_tc.cuh"
+#include "pq_tma.cuh"
+
+namespace pq {
+
+namespace {
+
+constexpr int BM = 128, BK = 32;
+constexpr int A_PLANE = BM * BK * 2;               // 8 KB
+constexpr int B_ATOM = BK * 128;                   // 4 KB: 32 k-rows x 64 columns
+constexpr int STAGE_A = 4 * A_PLANE;               // Arh Arl Aih Ail
+constexpr int N_EPI = 8;                           // epilogue warps
+constexpr int NTHREADS = 64 + 32 * N_EPI;
+constexpr uint64_t WAIT_NS = 2000000000ull;        // 2 s per wait
+
+// Tile geometry of the two variants: BNC complex output columns per tile.
+template <int BNC>
+struct Geo {
+  static constexpr int NBA = BNC / 64;             // 64-column atoms per B plane
+  static constexpr int B_PLANE = NBA * B_ATOM;
+  static constexpr int STAGE = STAGE_A + 4 * B_PLANE;  // + Brh Bih Brl Bil
+  static constexpr int NS = BNC == 128 ? 3 : 4;         // 192 KB of stages either way
+  static constexpr uint32_t ACC_COLS = 2 * BNC;         // Re in 0..BNC-1, Im in BNC..2 BNC-1
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // two accumulators
+  static constexpr size_t SMEM = (size_t)NS * STAGE + 1024;
+};
+
+// kind::f16 instruction descriptor: F32 accumulator, BF16 A and B, A K-major,
+// B MN-major, M = 128, optional negation of A.
+constexpr uint32_t idesc(int n, bool neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ uint64_t desc_a(uint32_t addr) { return tc::smem_desc(addr, 16, 512, 4); }
+__device__ __forceinline__ uint64_t desc_b(uint32_t addr) { return tc::smem_desc(addr, B_ATOM, 1024, 2); }
+
+struct Tile {
+  const BseProblem *p;
+  int z, row0, col0, kt;
+};
+
+// Tile t of the launch: the problem whose tile range holds t (binary search on tile0),
+// then GEMM, row block and column block within it (columns fastest).
+template <int BNC>
+__device__ __forceinline__ Tile decode(const BseProblem *__restrict__ probs, int nprob, long long t) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  Tile r;
+  r.p = probs + lo;
+  const int n = r.p->n, ntc = (n + BNC - 1) / BNC, per_z = ((n + BM - 1) / BM) * ntc;
+  const long long u = t - r.p->tile0;
+  r.z = (int)(u / per_z);
+  const int rem = (int)(u % per_z);
+  r.row0 = (rem / ntc) * BM;
+  r.col0 = (rem % ntc) * BNC;
+  r.kt = (n + BK - 1) / BK;
+  return r;
+}
+
+template <int BNC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    bse_bf16_tma_kernel(const BseProblem *__restrict__ probs, int nprob, long long tiles, int *err) {
+  using G = Geo<BNC>;
+  constexpr int NS = G::NS, STAGE = G::STAGE, B_PLANE = G::B_PLANE;
+  constexpr uint32_t ID_PAIR = idesc(2 * BNC, false), ID_ONE = idesc(BNC, false), ID_ONE_N = idesc(BNC, true);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], drain;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&acc_full[i], 1);
+      tc::mbar_init(&acc_empty[i], 32 * N_EPI);
+    }
+    tc::mbar_init(&drain, 1);
+    tc::mbar_fence_init();
+    for (int i = 0; i < nprob && i < 8; ++i) {
+      tma::prefetch_map(&probs[i].mapA);
+      tma::prefetch_map(&probs[i].mapB);
+    }
+  }
+  if (warp == 1) tc::tmem_alloc(&tslot, G::TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t sbase = tc::smem_u32(sm);
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ TMA producer
+      long long it = 0;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const Tile T = decode<BNC>(probs, nprob, t);
+        const CUtensorMap *mA = &T.p->mapA, *mB = &T.p->mapB;
+        for (int kt = 0; kt < T.kt; ++kt, ++it) {
+          const int s = (int)(it % NS);
+          if (it >= NS && !tc::mbar_wait_ns(&empty[s], (uint32_t)((it / NS - 1) & 1), WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          tma::mbar_expect_tx(&full[s], STAGE);
+          const uint32_t st = sbase + (uint32_t)(s * STAGE);
+          const int k0 = kt * BK;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) tma::load4(st + p * A_PLANE, mA, k0, T.row0, T.z, p, &full[s]);
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int at = 0; at < G::NBA; ++at)
+              tma::load4(st + STAGE_A + w * B_PLANE + at * B_ATOM, mB, T.col0 + 64 * at, k0, T.z, w, &full[s]);
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA exits
+        for (long long j = it > NS ? it - NS : 0; j < it; ++j)
+          tc::mbar_wait_ns(&full[j % NS], (uint32_t)((j / NS) & 1), WAIT_NS);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      long long it = 0;
+      int tl = 0;
+      bool issued = false;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+        const Tile T = decode<BNC>(probs, nprob, t);
+        const int b = tl & 1;
+        if (tl >= 2) {
+          if (!tc::mbar_wait_ns(&acc_empty[b], (uint32_t)(((tl >> 1) - 1) & 1), WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+        }
+        const uint32_t d = tmem + (uint32_t)b * G::ACC_COLS;
+        for (int kt = 0; kt < T.kt; ++kt, ++it) {
+          const int s = (int)(it % NS);
+          if (!tc::mbar_wait_ns(&full[s], (uint32_t)((it / NS) & 1), WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = sbase + (uint32_t)(s * STAGE), sb = sa + STAGE_A;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {  // two K = 16 steps per stage
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {  // (Ah, Bh), (Ah, Bl), (Al, Bh)
+              const int al = (pr == 2), bl = (pr == 1);
+              const uint64_t ar = desc_a(sa + al * A_PLANE + 32 * j);
+              const uint64_t ai = desc_a(sa + (2 + al) * A_PLANE + 32 * j);
+              const uint32_t bb = sb + 2 * bl * B_PLANE + 2048 * j;
+              const uint32_t acc = (kt | j | pr) ? 1u : 0u;
+              mma(d, ar, desc_b(bb), ID_PAIR, acc);              // Re += Ar Br, Im += Ar Bi
+              mma(d, ai, desc_b(bb + B_PLANE), ID_ONE_N, 1u);    // Re -= Ai Bi
+              mma(d + BNC, ai, desc_b(bb), ID_ONE, 1u);          // Im += Ai Br
+            }
+          }
+          tc::mma_commit(&empty[s]);
+          issued = true;
+        }
+        if (!ok) break;
+        tc::mma_commit(&acc_full[b]);
+      }
+      if (issued) {
+        // all MMAs of this CTA complete before tensor memory is released
+        tc::mma_commit(&drain);
+        if (!tc::mbar_wait_ns(&drain, 0, WAIT_NS)) ok = false;
+      }
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    constexpr int CW = BNC / 2;  // columns per epilogue warp (two warps per lane quarter)
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    int tl = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+      const int b = tl & 1;
+      if (!tc::mbar_wait_ns(&acc_full[b], (uint32_t)((tl >> 1) & 1), WAIT_NS)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const Tile T = decode<BNC>(probs, nprob, t);
+      const BseProblem &P = *T.p;
+      const int n = P.n, row = T.row0 + 32 * q + lane;
+      const float alpha = P.alpha, beta = 1.0f - alpha;
+      const long long slab = (long long)(T.z / P.zc) * P.phi_cs + P.phi_q0 + T.z % P.zc;
+      const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * G::ACC_COLS;
+#pragma unroll 1
+      for (int c = CW * half; c < CW * half + CW; c += 16) {
+        float cr[16], ci[16];
+        tc::tmem_ld16(tb + (uint32_t)c, cr);
+        tc::tmem_ld16(tb + (uint32_t)(BNC + c), ci);
+        if (row < n) {
+          const long long off = (slab * n + row) * (long long)n + T.col0 + c;
+          const float2 *pi = P.phi_in + off;
+          float2 *po = P.phi_out + off;
+          const int lim = n - (T.col0 + c);
+          if (lim >= 16) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+              float4 o = *reinterpret_cast<const float4 *>(pi + i);
+              o.x = alpha * cr[i] + beta * o.x;
+              o.y = alpha * ci[i] + beta * o.y;
+              o.z = alpha * cr[i + 1] + beta * o.z;
+              o.w = alpha * ci[i + 1] + beta * o.w;
+              *reinterpret_cast<float4 *>(po + i) = o;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (i < lim) {
+                const float2 o = pi[i];
+                po[i] = make_float2(alpha * cr[i] + beta * o.x, alpha * ci[i] + beta * o.y);
+              }
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive_cta(&acc_empty[b]);
+    }
+  }
+  if (!ok) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, G::TMEM_COLS);
+}
+
+}  // namespace
+
+size_t bse_tma_smem_bytes(int bnc) { return bnc == 64 ? Geo<64>::SMEM : Geo<128>::SMEM; }
+
+long long bse_tiles(int bnc, int n, int batch) {
+  return (long long)((n + BM - 1) / BM) * ((n + bnc - 1) / bnc) * batch;
+}
+
+// The encoder is a driver entry point; it is looked up through the runtime so that the
+// library itself does not link the driver (it loads on hosts without a GPU).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long long slabs, CUtensorMap *mapA,
+                       CUtensorMap *mapB) {
+  const PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = tensor_map_encoder();
+  if (!cuTensorMapEncodeTiled) return CUDA_ERROR_NOT_FOUND;
+  const cuuint64_t row = (cuuint64_t)ld * 2, mat = row * (cuuint64_t)n, plane = mat * (cuuint64_t)slabs;
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  {
+    // A: x = k (contiguous), y = row, z = GEMM, w = plane (Arh, Arl, Aih, Ail)
+    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)slabs, 4};
+    const cuuint64_t str[3] = {row, mat, plane};
+    const cuuint32_t box[4] = {BK, BM, 1, 1};
+    CUresult r = cuTensorMapEncodeTiled(mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, gam_planes, dims, str, box, es,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return r;
+  }
+  {
+    // B: x = column (contiguous), y = k, z = GEMM, w = plane (Brh, Bih, Brl, Bil, Brr, Bir)
+    const cuuint64_t dims[4] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)slabs, 6};
+    const cuuint64_t str[3] = {row, mat, plane};
+    const cuuint32_t box[4] = {64, BK, 1, 1};
+    return cuTensorMapEncodeTiled(mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, fv_planes, dims, str, box, es,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+}
+
+cudaError_t launch_bse_tma(cudaStream_t st, int bnc, const BseProblem *probs, int nprob, long long tiles,
+                           int *err, int max_ctas) {
+  if (tiles <= 0 || nprob <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
+  const unsigned grid = (unsigned)std::min<long long>(tiles, sms);
+  if (bnc == 64) {
+    e = cudaFuncSetAttribute(bse_bf16_tma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<64>::SMEM);
+    if (e != cudaSuccess) return e;
+    bse_bf16_tma_kernel<64><<<grid, NTHREADS, Geo<64>::SMEM, st>>>(probs, nprob, tiles, err);
+  } else {
+    e = cudaFuncSetAttribute(bse_bf16_tma_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geo<128>::SMEM);
+    if (e != cudaSuccess) return e;
+    bse_bf16_tma_kernel<128><<<grid, NTHREADS, Geo<128>::SMEM, st>>>(probs, nprob, tiles, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pq

@@ -1,12 +1,11 @@
-// Split-precision Bethe-Salpeter products on the tcgen05 tensor cores.
+// TF32x3 Bethe-Salpeter products on the tcgen05 tensor cores, from complex64 operands.
 //
 // For every (r, Q) the BSE (App. A, Eq. PA_F_Phi) is one complex n x n x n
 // product C = A B with A = s_r Gamma_r(Q) diag(X_r(Q)) and B = F_r(Q), both
 // complex64, and the mixing Phi <- alpha C + (1 - alpha) Phi in the epilogue.
-// Each FP32 operand x is split into low-precision parts and a real product X Y
-// is taken over the leading part products, with FP32 accumulation:
-//   TF32x3: x = h + l (h TF32, l read as TF32), XY ~ Xh Yh + Xh Yl + Xl Yh   (~2^-22 per product)
-//   BF16x3: x = h + l (BF16), same three products                  (~2^-16 per product)
+// Each FP32 operand x is split into x = h + l (h TF32, l read as TF32) inside
+// this kernel, and a real product XY is taken as Xh Yh + Xh Yl + Xl Yh with FP32
+// accumulation (~2^-22 per product).
 //
 // Complex arithmetic as two real products into one 128 x 256 accumulator:
 // the B tile is staged as 384 K-major rows [-Bi ; Br ; Bi], so
@@ -19,10 +18,8 @@
 // (tcgen05.st), so the MMAs read A there and only B from 64-byte-swizzled
 // shared memory.  Eight producer warps fetch raw complex64 tiles with cp.async,
 // convert them and stage the planes; one warp issues the MMAs; stages hand
-// over through mbarriers, and tcgen05.commit releases each stage.  Both
-// schemes use 64-byte operand rows: 16 k per stage for TF32, 32 for BF16.
-#include <cuda_bf16.h>
-
+// over through mbarriers, and tcgen05.commit releases each stage.  Operand rows
+// are 64 bytes: 16 k per stage.
 #include "pq_common.cuh"
 #include "pq_internal.h"
 #include "pq_tc.cuh"
@@ -39,7 +36,7 @@ constexpr uint32_t D_COLS = 2 * BNC;     // accumulator: Re in 0..127, Im in 128
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t WAIT_TRIES = 1u << 24;
 
-enum Scheme { TF32X3 = 0, BF16X3 = 1 };
+enum Scheme { TF32X3 = 0 };
 
 template <int SC>
 struct Traits;
@@ -49,14 +46,6 @@ struct Traits<TF32X3> {
   static constexpr int KG = 4;     // k per 16-byte chunk of a staged row
   static constexpr int NRAW = 3;   // raw stages: cp.async two stages ahead
   static constexpr uint32_t IDESC = tc::idesc_tf32(BM, 2 * BNC, false);
-};
-template <>
-struct Traits<BF16X3> {
-  static constexpr int BK = 32;    // 32 x 2 B = one 64-byte row
-  static constexpr int KG = 8;
-  static constexpr int NRAW = 2;   // one stage ahead (shared memory holds two 64 KB raw stages)
-  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * BNC >> 3) << 17) |
-                                    ((uint32_t)(BM >> 4) << 24);  // F32 accumulate, BF16 A and B
 };
 
 template <int SC>
@@ -84,25 +73,8 @@ __device__ __forceinline__ void split_tf32(float x, float &h, float &l) {
   h = tc::to_tf32(x);
   l = x - h;
 }
-__device__ __forceinline__ void split_bf16(float x, float &h, float &l) {
-  h = __bfloat162float(__float2bfloat16_rn(x));
-  l = x - h;  // exact; rounded to BF16 when packed
-}
-// two consecutive-k values packed as one 32-bit word, the even k in the low half
-__device__ __forceinline__ uint32_t pack_bf16(float even, float odd) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(even, odd);
-  return *reinterpret_cast<uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_tmem_a(int sc, uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (sc == TF32X3) {
-    tc::mma_tf32_tmem_a(d, a, b, idesc, acc);
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
-        "r"(a), "l"(b), "r"(idesc), "r"(acc));
-  }
+__device__ __forceinline__ void mma_tmem_a(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  tc::mma_tf32_tmem_a(d, a, b, idesc, acc);
 }
 
 __device__ __forceinline__ void cp_async_mbar_arrive(void *bar) {
@@ -120,7 +92,6 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
   using Tr = Traits<SC>;
   using Ly = Layout<SC>;
   constexpr int BK = Tr::BK, KG = Tr::KG, NRAW = Tr::NRAW;
-  constexpr bool BF = (SC == BF16X3);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t raw_full[NRAW], raw_empty[NRAW], split_full[NSTAGE], split_empty[NSTAGE], done;
@@ -169,13 +140,13 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
           auto d = [&](uint32_t b) { return tc::smem_desc(b + o, 16, 512, 4); };
           const uint32_t acc0 = (kt > 0 || j > 0) ? 1u : 0u;
           // D += Ar [Br | Bi]: B rows 128..383
-          mma_tmem_a(SC, tmem, arh + ak, d(bh + B_BLOCK), Tr::IDESC, acc0);
-          mma_tmem_a(SC, tmem, arh + ak, d(bl + B_BLOCK), Tr::IDESC, 1u);
-          mma_tmem_a(SC, tmem, arl + ak, d(bh + B_BLOCK), Tr::IDESC, 1u);
+          mma_tmem_a(tmem, arh + ak, d(bh + B_BLOCK), Tr::IDESC, acc0);
+          mma_tmem_a(tmem, arh + ak, d(bl + B_BLOCK), Tr::IDESC, 1u);
+          mma_tmem_a(tmem, arl + ak, d(bh + B_BLOCK), Tr::IDESC, 1u);
           // D += Ai [-Bi | Br]: B rows 0..255
-          mma_tmem_a(SC, tmem, aih + ak, d(bh), Tr::IDESC, 1u);
-          mma_tmem_a(SC, tmem, aih + ak, d(bl), Tr::IDESC, 1u);
-          mma_tmem_a(SC, tmem, ail + ak, d(bh), Tr::IDESC, 1u);
+          mma_tmem_a(tmem, aih + ak, d(bh), Tr::IDESC, 1u);
+          mma_tmem_a(tmem, aih + ak, d(bl), Tr::IDESC, 1u);
+          mma_tmem_a(tmem, ail + ak, d(bh), Tr::IDESC, 1u);
         }
         tc::mma_commit(&split_empty[s]);
         if (kt == KT - 1) tc::mma_commit(&done);
@@ -237,27 +208,15 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
       const unsigned char *ra = raw0 + r_ * Ly::RAW, *rb = ra + Ly::RAW_A;
       // ---- A: this thread's row, BK/2 complex values -> 8 TMEM columns of each plane
       {
-        float rh[8], rl[8], ih[8], il[8];  // TF32: one value per column; BF16: packed pairs
+        float rh[8], rl[8], ih[8], il[8];  // one value per TMEM column
 #pragma unroll
         for (int i = 0; i < BK / 4; ++i) {
           const int c = a_kh * (BK / 4) + i;
           const float4 v = *reinterpret_cast<const float4 *>(ra + a_row * Ly::RAW_A_ROW + ((c ^ (a_row & 7)) << 4));
-          float h0, l0, h1, l1, h2, l2, h3, l3;
-          if (BF) {
-            split_bf16(v.x, h0, l0);
-            split_bf16(v.y, h1, l1);
-            split_bf16(v.z, h2, l2);
-            split_bf16(v.w, h3, l3);
-            rh[i] = __uint_as_float(pack_bf16(h0, h2));
-            rl[i] = __uint_as_float(pack_bf16(l0, l2));
-            ih[i] = __uint_as_float(pack_bf16(h1, h3));
-            il[i] = __uint_as_float(pack_bf16(l1, l3));
-          } else {
-            split_tf32(v.x, rh[2 * i], rl[2 * i]);
-            split_tf32(v.y, ih[2 * i], il[2 * i]);
-            split_tf32(v.z, rh[2 * i + 1], rl[2 * i + 1]);
-            split_tf32(v.w, ih[2 * i + 1], il[2 * i + 1]);
-          }
+          split_tf32(v.x, rh[2 * i], rl[2 * i]);
+          split_tf32(v.y, ih[2 * i], il[2 * i]);
+          split_tf32(v.z, rh[2 * i + 1], rl[2 * i + 1]);
+          split_tf32(v.w, ih[2 * i + 1], il[2 * i + 1]);
         }
         const uint32_t t = tmem + a_lane + D_COLS + (uint32_t)s * Ly::A_STAGE_COLS + 8u * a_kh;
         tc::tmem_st8(t, rh);
@@ -278,22 +237,7 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
         const int cc = t ^ b_glo;
         const int col = 2 * b_p + cc;
         uint4 rh, rl, ih, il, nih, nil;
-        if (BF) {
-          float h[8], l[8], hi[8], li[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            split_bf16(cc ? rbv[j].z : rbv[j].x, h[j], l[j]);
-            split_bf16(cc ? rbv[j].w : rbv[j].y, hi[j], li[j]);
-          }
-          rh = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-          rl = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
-          ih = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
-                          pack_bf16(hi[6], hi[7]));
-          il = make_uint4(pack_bf16(li[0], li[1]), pack_bf16(li[2], li[3]), pack_bf16(li[4], li[5]),
-                          pack_bf16(li[6], li[7]));
-          nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
-          nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
-        } else {
+        {
           float h[4], l[4], hi[4], li[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -365,22 +309,15 @@ __global__ void __launch_bounds__(NT + 32, 1) bse_split_kernel(int n, const floa
 
 }  // namespace
 
-size_t bse_tc_smem_bytes(int scheme) { return scheme == BF16X3 ? Layout<BF16X3>::SMEM : Layout<TF32X3>::SMEM; }
+size_t bse_tc_smem_bytes() { return Layout<TF32X3>::SMEM; }
 
-cudaError_t launch_bse_split(cudaStream_t st, int scheme, int n, int batch, const float2 *A, const float2 *B,
-                             float2 *Phi, float alpha, int *err) {
-  const size_t sm = bse_tc_smem_bytes(scheme);
+cudaError_t launch_bse_split(cudaStream_t st, int n, int batch, const float2 *A, const float2 *B, float2 *Phi,
+                             float alpha, int *err) {
+  const size_t sm = bse_tc_smem_bytes();
   dim3 grid((n + BNC - 1) / BNC, (n + BM - 1) / BM, batch);
-  cudaError_t e;
-  if (scheme == BF16X3) {
-    e = cudaFuncSetAttribute(bse_split_kernel<BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    bse_split_kernel<BF16X3><<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
-  } else {
-    e = cudaFuncSetAttribute(bse_split_kernel<TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    bse_split_kernel<TF32X3><<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
-  }
+  cudaError_t e = cudaFuncSetAttribute(bse_split_kernel<TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  bse_split_kernel<TF32X3><<<grid, NT + 32, sm, st>>>(n, A, B, Phi, alpha, err);
   return cudaGetLastError();
 }
 

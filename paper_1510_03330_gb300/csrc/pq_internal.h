@@ -1,6 +1,7 @@
 // Host-side launchers shared by the translation units of the solver.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "pq_common.cuh"
@@ -44,6 +45,24 @@ struct Buffers {
   double2 *chi = nullptr;        // [4][nQ]
   double2 *gemm_work = nullptr;  // split-K partials of the Sigma~1 transforms
   long long gemm_work_elems = 0;
+  // Storage of the BSE operands gam and fv:
+  //   V_C128 / V_C64: [r][Q][k][ld] complex of the storage type;
+  //   V_BF16P: BF16 planes [plane][r][Q][k][ld]; gam planes (Re h, Re l, Im h, Im l),
+  //   fv planes (Re h, Im h, Re l, Im l, Re r, Im r) with x = h + l + r.
+  int vfmt = 0;
+  int ld = 0;                    // row stride of gam and fv (elements)
+  int q_chunk = 0;               // q-momenta assembled and multiplied per pass
+  void *phi_new = nullptr;       // Jacobi target when the transfers run in several passes
+};
+
+enum VFmt { V_C128 = 0, V_C64 = 1, V_BF16P = 2 };
+
+// One pass of the assembly and the BSE over the transfers Q = (q, m) with
+// q-momentum in [qb, qb + nq): the operand buffers hold 4 * nq * NOmega slices.
+struct Pass {
+  int qb, nq;
+  bool fused;       // nq == nk: d/m and s/t outputs of one gather step written together
+  bool accumulate;  // add to the dF part of Sigma instead of overwriting it
 };
 
 // Pointers of one Sigma~1 evaluation (the context's buffers, or a caller's scratch).
@@ -78,18 +97,40 @@ cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const 
 Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *out);
 cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1);
 cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b);
-cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
+// chi of the slices in the operand buffers (q-momenta [qb, qb + nq))
+cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int nq);
 
 // vertex steps (pq_vertex.cu)
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
-cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64, const double *lam4);
+cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p);
 size_t assemble_smem_bytes(const Grid &g, bool c64);
 
-// split-precision BSE on the tensor cores (pq_gemm_tc.cu)
-// scheme: 0 TF32x3, 1 BF16x3
-size_t bse_tc_smem_bytes(int scheme);
-cudaError_t launch_bse_split(cudaStream_t st, int scheme, int n, int batch, const float2 *A, const float2 *B,
-                             float2 *Phi, float alpha, int *err);
+// TF32x3 BSE on the tensor cores from complex64 operands (pq_gemm_tc.cu)
+size_t bse_tc_smem_bytes();
+cudaError_t launch_bse_split(cudaStream_t st, int n, int batch, const float2 *A, const float2 *B, float2 *Phi,
+                             float alpha, int *err);
+
+// BF16x3 BSE from pre-split planes, fed by TMA (pq_bse_tma.cu).  One launch covers the tiles of
+// one or more problems (a context's pass, or the solves of a batch), described by a device table.
+// GEMM z of a problem reads operand slice z and updates Phi slice
+// (z / zc) * phi_cs + phi_q0 + z % zc.
+struct BseProblem {
+  CUtensorMap mapA;   // Gamma X planes [plane][slice][row][ld]
+  CUtensorMap mapB;   // F planes
+  long long tile0;    // first tile of this problem within the launch
+  int n, batch, zc, pad_;
+  long long phi_cs, phi_q0;
+  const float2 *phi_in;
+  float2 *phi_out;
+  float alpha;
+};
+size_t bse_tma_smem_bytes(int bnc);
+long long bse_tiles(int bnc, int n, int batch);
+CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long long slabs, CUtensorMap *mapA,
+                       CUtensorMap *mapB);
+// bnc: complex output columns per tile (128 or 64); max_ctas > 0 caps the persistent grid
+cudaError_t launch_bse_tma(cudaStream_t st, int bnc, const BseProblem *probs, int nprob, long long tiles,
+                           int *err, int max_ctas);
 
 // Sigma~2 (pq_sigma2.cu)
 cudaError_t launch_sigma2(cudaStream_t st, const Grid &g, const Sizes &z, Buffers &b);

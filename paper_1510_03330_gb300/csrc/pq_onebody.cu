@@ -5,6 +5,8 @@
 // All arithmetic here is FP64.
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
 #include "pq_common.cuh"
 #include "pq_internal.h"
 
@@ -148,19 +150,41 @@ __global__ void sigma_update_kernel(Grid g, const double2 *__restrict__ s1, cons
   }
 }
 
-// chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k'); one block per (r, Q).
-template <typename S>
-__global__ void chi_kernel(Grid g, const S *__restrict__ fv, const double2 *__restrict__ xph,
-                           const double2 *__restrict__ xpp, double2 *__restrict__ chi) {
+// Element e of the F operand buffer as a double2: one complex of the storage type,
+// or the sum of the three BF16 pieces of the planes (Re h, Im h, Re l, Im l, Re r, Im r).
+template <int FMT>
+__device__ inline double2 f_elem(const void *fv, long long ps, long long e) {
+  if constexpr (FMT == V_C128) {
+    return ((const double2 *)fv)[e];
+  } else if constexpr (FMT == V_C64) {
+    const float2 v = ((const float2 *)fv)[e];
+    return make_double2(v.x, v.y);
+  } else {
+    const __nv_bfloat16 *p = (const __nv_bfloat16 *)fv;
+    return make_double2((double)__bfloat162float(p[e]) + (double)__bfloat162float(p[2 * ps + e]) +
+                            (double)__bfloat162float(p[4 * ps + e]),
+                        (double)__bfloat162float(p[ps + e]) + (double)__bfloat162float(p[3 * ps + e]) +
+                            (double)__bfloat162float(p[5 * ps + e]));
+  }
+}
+
+// chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k'); one block per (r, Q) of the
+// slices in the operand buffer (nq q-momenta from qb).
+template <int FMT>
+__global__ void chi_kernel(Grid g, const void *__restrict__ fv, int ld, int qb, int nq, int q_chunk,
+                           const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
+                           double2 *__restrict__ chi) {
   __shared__ double2 red[256];
-  int r = blockIdx.y, Q = blockIdx.x;
+  const int r = blockIdx.y, Ql = blockIdx.x, Q = qb * g.n_om + Ql;
+  const long long slabs = (long long)nq * g.n_om;                      // slices per channel in this pass
+  const long long ps = 4LL * q_chunk * g.n_om * g.n * (long long)ld;   // plane stride of the buffer
   const double2 *X = (r < 2 ? xph : xpp) + (long long)Q * g.n;
-  const S *F = fv + ((long long)r * g.nQ + Q) * g.n * g.n;
+  const long long base = ((long long)r * slabs + Ql) * g.n * (long long)ld;
   double2 acc = make_double2(0.0, 0.0);
   int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   for (int k = warp; k < g.n; k += nw) {
     double2 rs = make_double2(0.0, 0.0);
-    for (int kp = lane; kp < g.n; kp += 32) rs = cfma(to_c<S, double2>(F[(long long)k * g.n + kp]), X[kp], rs);
+    for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem<FMT>(fv, ps, base + (long long)k * ld + kp), X[kp], rs);
     acc = cfma(X[k], rs, acc);
     if (lane == 0) acc = acc + X[k];
   }
@@ -242,12 +266,14 @@ cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, bool c64) {
-  dim3 grid(g.nQ, 4);
-  if (c64)
-    chi_kernel<float2><<<grid, 256, 0, st>>>(g, (const float2 *)b.fv, b.xph, b.xpp, b.chi);
+cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int nq) {
+  dim3 grid(nq * g.n_om, 4);
+  if (b.vfmt == V_C128)
+    chi_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
+  else if (b.vfmt == V_C64)
+    chi_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
   else
-    chi_kernel<double2><<<grid, 256, 0, st>>>(g, (const double2 *)b.fv, b.xph, b.xpp, b.chi);
+    chi_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
   return cudaGetLastError();
 }
 

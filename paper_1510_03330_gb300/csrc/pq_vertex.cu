@@ -17,6 +17,8 @@
 //   S_x = Psi_x[(q', .)][k][(k', .)]       x = s, t   (map B, own s/t)
 // with q' = k + k' + q, and writes the d/m outputs at transfer q and the s/t
 // outputs at transfer q'.  Every element of Phi is read exactly once.
+#include <cuda_bf16.h>
+
 #include "pq_common.cuh"
 #include "pq_internal.h"
 
@@ -82,22 +84,64 @@ template <> __device__ inline float2 cz<float2>() { return make_float2(0.f, 0.f)
 template <typename C> __device__ inline C cfrom(double2 v);
 template <> __device__ inline double2 cfrom<double2>(double2 v) { return v; }
 template <> __device__ inline float2 cfrom<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
-template <typename C, typename S> __device__ inline S cstore(C v);
-template <> __device__ inline double2 cstore<double2, double2>(double2 v) { return v; }
-template <> __device__ inline float2 cstore<float2, float2>(float2 v) { return v; }
 template <typename C> __device__ inline double2 cdbl(C v);
 template <> __device__ inline double2 cdbl<double2>(double2 v) { return v; }
 template <> __device__ inline double2 cdbl<float2>(float2 v) { return make_double2(v.x, v.y); }
 
-// S: storage type of vertices, C: arithmetic type (double2 for FP64, float2 for the split path).
-template <typename S, typename C>
-__global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restrict__ phi, S *__restrict__ gam,
-                                                       S *__restrict__ fv, const double2 *__restrict__ k1,
+// BF16 operand planes of the split BSE: x = h + l (+ r for F), each piece the
+// BF16 rounding of what the previous pieces leave (the differences are exact in FP32).
+__device__ inline void store_planes2(__nv_bfloat16 *p, long long ps, long long o, float2 v) {
+  const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+  p[o] = rh;
+  p[ps + o] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+  p[2 * ps + o] = ih;
+  p[3 * ps + o] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+}
+__device__ inline void store_planes3(__nv_bfloat16 *p, long long ps, long long o, float2 v) {
+  const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+  const float rr = v.x - __bfloat162float(rh), ir = v.y - __bfloat162float(ih);
+  const __nv_bfloat16 rl = __float2bfloat16_rn(rr), il = __float2bfloat16_rn(ir);
+  p[o] = rh;
+  p[ps + o] = ih;
+  p[2 * ps + o] = rl;
+  p[3 * ps + o] = il;
+  p[4 * ps + o] = __float2bfloat16_rn(rr - __bfloat162float(rl));
+  p[5 * ps + o] = __float2bfloat16_rn(ir - __bfloat162float(il));
+}
+
+template <typename S, bool PL>
+struct Out {
+  void *gam, *fv;
+  long long ps;  // plane stride (PL)
+  __device__ inline void put(long long o, float2 ga, float2 f) const {
+    if constexpr (PL) {
+      store_planes2((__nv_bfloat16 *)gam, ps, o, ga);
+      store_planes3((__nv_bfloat16 *)fv, ps, o, f);
+    } else {
+      ((S *)gam)[o] = ga;
+      ((S *)fv)[o] = f;
+    }
+  }
+  __device__ inline void put(long long o, double2 ga, double2 f) const {
+    ((S *)gam)[o] = ga;
+    ((S *)fv)[o] = f;
+  }
+};
+
+// S: storage type of vertices, C: arithmetic type (double2 for FP64, float2 for the split path);
+// PL: operands written as BF16 planes.
+// Pass p covers the output transfers with q-momentum in [p.qb, p.qb + p.nq); the operand
+// buffers hold their 4 * nq * NOmega slices with rows of ld elements.  A fused pass (all
+// momenta) writes the d/m outputs at q and the s/t outputs at q' = k + k' + q of one gather
+// step; otherwise each target momentum takes two gather steps, one per channel pair.
+template <typename S, typename C, bool PL>
+__global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restrict__ phi, Out<S, PL> out, int ld,
+                                                       const double2 *__restrict__ k1,
                                                        const double2 *__restrict__ k2row,
                                                        const double2 *__restrict__ xph,
                                                        const double2 *__restrict__ xpp,
                                                        const double2 *__restrict__ gtab, double2 *__restrict__ dfpart,
-                                                       Lam lam) {
+                                                       Lam lam, Pass pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.n_om * g.n_nu;
   // R blocks are read along columns (map A) and anti-diagonals (map C): rows padded by two
@@ -116,8 +160,8 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
   const int ikp = blockIdx.x, k = blockIdx.y;
   const int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
   const long long nn = g.n;
-  const long long slab = nn * nn;  // one (r, Q) matrix
-  const long long chan = (long long)g.nQ * slab;
+  const long long chan = (long long)g.nQ * nn * nn;                        // channel stride of Phi
+  const long long ochan = (long long)pass.nq * g.n_om * nn * ld;            // channel stride of the outputs
   const int tmom = ksub(g, ikp, ik);
   const double2 *xph_ = xph, *xpp_ = xpp;
 
@@ -133,7 +177,12 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
   const C twoU = cfrom<C>(U2);
   C acc = cz<C>();
 
-  for (int iq = 0; iq < g.nk; ++iq) {
+  const int nstep = pass.fused ? 1 : 2;
+  for (int iqc = pass.qb; iqc < pass.qb + pass.nq; ++iqc)
+  for (int step = 0; step < nstep; ++step) {
+    const bool do_dm = pass.fused || step == 0, do_st = pass.fused || step == 1;
+    // step 1 gathers for the s/t outputs at q' = iqc, i.e. from q = q' - k - k'
+    const int iq = step == 0 ? iqc : ksub(g, ksub(g, iqc, ik), ikp);
     const int iqp = kadd(g, kadd(g, ik, ikp), iq);
     const int cmom = kadd(g, ik, iq);
     const int pqk = ksub(g, iqp, ik);  // momentum of q' - k
@@ -154,10 +203,11 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
     for (int e = threadIdx.x; e < NB; e += blockDim.x) {
       const int mi = e / g.n_nu, npi = e % g.n_nu;
       const int m = g.m_lo + mi, np_ = g.n_lo + npi;
-      // ---------------- d/m at Q = (q, m)
       const int mt = np_ - n;  // transfer k' - k of maps A and C
       const bool inT = (mt >= g.m_lo && mt <= g.m_hi);
       const int ti = mt - g.m_lo;
+      if (do_dm) {
+      // ---------------- d/m at Q = (q, m)
       C Ad = cz<C>(), Am = cz<C>();
       const int nc = n + m;  // column k + q of map A
       if (inT) {
@@ -180,16 +230,15 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const C Gm = l1 + (-0.5f) * Ad + 0.5f * Am + (-0.5f) * Bs + 0.5f * Bt;
       const C Fd = Gd + od, Fm = Gm + om;
       const int Q = iq * g.n_om + mi;
-      const long long o_dm = ((long long)Q * nn + k) * nn + ikp * g.n_nu + npi;
+      const long long o_dm = ((long long)(Q - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
       const C xq = cfrom<C>(xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
-      gam[o_dm] = cstore<C, S>(cmul(Gd, xq));
-      gam[chan + o_dm] = cstore<C, S>(cmul(Gm, xq));
-      fv[o_dm] = cstore<C, S>(Fd);
-      fv[chan + o_dm] = cstore<C, S>(Fm);
+      out.put(o_dm, cmul(Gd, xq), Fd);
+      out.put(ochan + o_dm, cmul(Gm, xq), Fm);
       // Eq. PA_Sigma, ph part: G(k+q) X_ph(Q,k') [F_d - F_m - (Lambda0_d - Lambda0_m)]
       const C gkq = cfrom<C>(gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
       acc = cfma(cmul(gkq, xq), Fd - Fm - twoU, acc);
-
+      }
+      if (do_st) {
       // ---------------- s/t at Q' = (q', m)
       C Cd = cz<C>(), Cm = cz<C>();
       const int nc2 = m - np_ - 1;  // column q' - k' of map C
@@ -213,15 +262,14 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const C Gt = l3 + (-0.5f) * Cd + (-0.5f) * Cm + 0.5f * Dd + 0.5f * Dm;
       const C Fs = Gs + os, Ft = Gt + ot;
       const int Qp = iqp * g.n_om + mi;
-      const long long o_st = ((long long)Qp * nn + k) * nn + ikp * g.n_nu + npi;
+      const long long o_st = ((long long)(Qp - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
       const C xqp = cfrom<C>(xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
-      gam[2 * chan + o_st] = cstore<C, S>((-0.5f) * cmul(Gs, xqp));
-      gam[3 * chan + o_st] = cstore<C, S>(0.5f * cmul(Gt, xqp));
-      fv[2 * chan + o_st] = cstore<C, S>(Fs);
-      fv[3 * chan + o_st] = cstore<C, S>(Ft);
+      out.put(2 * ochan + o_st, (-0.5f) * cmul(Gs, xqp), Fs);
+      out.put(3 * ochan + o_st, 0.5f * cmul(Gt, xqp), Ft);
       // pp part: G(q'-k) X_pp(Q',k') [F_s + F_t - (Lambda0_s + Lambda0_t)]
       const C gqk = cfrom<C>(gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
       acc = cfma(cmul(gqk, xqp), Fs + Ft - twoU, acc);
+      }
     }
   }
   red[threadIdx.x] = cdbl<C>(acc);
@@ -233,7 +281,9 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
   if (threadIdx.x == 0) {
     // -(U/4)(T/N)^2 sum GGG: one T/N sits in X
     double pref = -(g.U * 0.25) * g.T / g.nk;
-    dfpart[(long long)k * g.nk + ikp] = pref * red[0];
+    double2 v = pref * red[0];
+    if (pass.accumulate) v = v + dfpart[(long long)k * g.nk + ikp];
+    dfpart[(long long)k * g.nk + ikp] = v;
   }
 }
 
@@ -253,26 +303,29 @@ cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, b
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, bool c64, const double *lam4) {
+template <typename S, typename C, bool PL>
+static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, Lam lam, const Pass &p, long long ps) {
+  auto kfn = assemble_kernel<S, C, PL>;
+  const size_t sm = assemble_smem_bytes(g, sizeof(S) == sizeof(float2));
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  Out<S, PL> out{b.gam, b.fv, ps};
+  kfn<<<dim3(g.nk, g.n), 256, sm, st>>>(g, (const S *)b.phi, out, b.ld, b.k1, b.k2row, b.xph, b.xpp, b.gtab,
+                                        b.dfpart, lam, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p) {
   Lam lam;
   for (int r = 0; r < 4; ++r) lam.l[r] = make_double2(lam4[2 * r], lam4[2 * r + 1]);
-  dim3 grid(g.nk, g.n);
-  size_t sm = assemble_smem_bytes(g, c64);
-  cudaError_t e;
-  if (c64) {
-    auto kfn = assemble_kernel<float2, float2>;
-    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    kfn<<<grid, 256, sm, st>>>(g, (const float2 *)b.phi, (float2 *)b.gam, (float2 *)b.fv, b.k1, b.k2row, b.xph,
-                               b.xpp, b.gtab, b.dfpart, lam);
-  } else {
-    auto kfn = assemble_kernel<double2, double2>;
-    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    kfn<<<grid, 256, sm, st>>>(g, (const double2 *)b.phi, (double2 *)b.gam, (double2 *)b.fv, b.k1, b.k2row, b.xph,
-                               b.xpp, b.gtab, b.dfpart, lam);
+  // plane stride: fixed by the buffer size (q_chunk momenta), which the tensor maps assume,
+  // also for a last pass with fewer momenta
+  const long long ps = 4LL * b.q_chunk * g.n_om * g.n * (long long)b.ld;
+  switch (b.vfmt) {
+    case V_C128: return assemble_launch<double2, double2, false>(st, g, b, lam, p, ps);
+    case V_C64: return assemble_launch<float2, float2, false>(st, g, b, lam, p, ps);
+    default: return assemble_launch<float2, float2, true>(st, g, b, lam, p, ps);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace pq

@@ -92,6 +92,29 @@ CONFIGS = {
 }
 
 
+def batch_draw(seed: int = 1510, count: int = 64) -> list[Params]:
+    """The seeded batch of uneven solves: square lattices with L ~ U{2..6}, Nnu ~ U{8, 16, 24, 32}
+    (NOmega = Nnu), U ~ U[0.5, 3], beta ~ U[2, 10], half filling; numpy PCG64 with the given seed,
+    drawn in the order (L, Nnu, U, beta) solve by solve."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        L = int(rng.integers(2, 7))
+        nu = int(rng.choice([8, 16, 24, 32]))
+        U = float(rng.uniform(0.5, 3.0))
+        beta = float(rng.uniform(2.0, 10.0))
+        out.append(Params(SQUARE, beta=beta, U=U, mu=0.0, L=L, n_nu=nu, n_Omega=nu))
+    return out
+
+
+def device_bytes_bf16x3(p: Params) -> int:
+    """Device memory of a single-pass PQ_SPLIT_BF16X3 solve: Phi (complex64, 8 bytes per element)
+    and the BSE operand planes (8 + 12 bytes per element; rows padded to 8 elements), plus the
+    one-particle and self-energy tables (bounded by 128 MB at the default quadrature)."""
+    ld = (p.n + 7) // 8 * 8
+    return 4 * p.n_Q * p.n * (8 * p.n + 20 * ld) + (128 << 20)
+
+
 def random_state(p: Params, seed: int, amplitude: float | None = None):
     """Seeded synthetic reducible vertex and self-energy of the paper's shape.
 

@@ -67,3 +67,28 @@ def test_null_context_calls_are_safe(lib):
     assert lib.pq_iterate(None, 1, 0.0, None, None) == binding.PQ_EINVAL
     lib.pq_destroy(None)
     assert lib.pq_step_name(0) == b"dyson"
+
+
+def test_bad_q_chunk_is_rejected(lib):
+    o = binding.default_options()
+    o.q_chunk = -1
+    h = C.c_void_p()
+    assert lib.pq_init(C.byref(h), 1, 2.0, 1.0, 0.0, 2, 8, 7, C.byref(o)) == binding.PQ_EINVAL
+    assert "q_chunk" in lib.pq_last_error(None).decode()
+
+
+def test_batch_arguments_are_checked_without_touching_the_gpu(lib):
+    o = binding.BatchOptions()
+    lib.pq_batch_default_options(C.byref(o))
+    assert (o.tile_cols, o.order, o.time_steps) == (0, -1, 0)
+    h = C.c_void_p()
+    assert lib.pq_batch_create(C.byref(h), None, 0, None) == binding.PQ_EINVAL
+    assert not h.value
+    arr = (C.c_void_p * 1)(None)
+    assert lib.pq_batch_create(C.byref(h), arr, 1, None) == binding.PQ_EINVAL
+    assert "NULL" in lib.pq_last_error(None).decode()
+    o.tile_cols = 96
+    assert lib.pq_batch_create(C.byref(h), arr, 1, C.byref(o)) == binding.PQ_EINVAL
+    assert "tile_cols" in lib.pq_last_error(None).decode()
+    assert lib.pq_batch_iterate(None, 1, None) == binding.PQ_EINVAL
+    lib.pq_batch_destroy(None)
