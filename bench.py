@@ -41,7 +41,7 @@ DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulat
          SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
 # DRAM bytes of one launch / algorithmic bytes, from ncu captures on the 4x4 lattice
 # (profiles/bse_*_square4_u2_b5.md, profiles/assemble_*_square4_u2_b5.md)
-BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
+BSE_TRAFFIC = {SPLIT_TF32X3: 0.986, SPLIT_BF16X3: 0.978}
 REMAP_TRAFFIC = {FP64: 1.112, SPLIT_TF32X3: 1.052}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
@@ -278,6 +278,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(CONFIGS) + [BATCH])
     ap.add_argument("--precision", default=DEFAULT_PRECISION,
                     choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_BF16X6])
+    ap.add_argument("--q-chunk", type=int, default=0,
+                    help="q-momenta per pass of the iteration (0: all that fit in device memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -298,6 +300,8 @@ def main():
     else:
         p = CONFIGS[a.workload]
         cfg = describe(a.workload, p, a.precision)
+    if a.q_chunk:
+        cfg["q_chunk"] = a.q_chunk
     cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
 
     if a.impl == "reference":
@@ -396,7 +400,7 @@ def main():
         return {"iterations": 2, "sigma_rel_err": relerr(sol.sigma(), ref_sig),
                 "F_m_rel_err": relerr(sol.F(1, p.n_Q // 2), ref_F), "chi_m_rel_err": relerr(sol.chi(1), ref_chi)}
 
-    solver = Solver(p, precision=a.precision, time_steps=True)
+    solver = Solver(p, precision=a.precision, time_steps=True, q_chunk=a.q_chunk)
     if compare is not None:
         solver.iterate(2)
         compare.update(errors_vs_fp64(solver))
@@ -509,7 +513,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        s = Solver(p, precision=a.precision)
+        s = Solver(p, precision=a.precision, q_chunk=a.q_chunk)
         for _ in range(a.steps):
             s.iterate(1)
             sig = s.sigma()

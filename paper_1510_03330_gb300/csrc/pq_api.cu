@@ -222,20 +222,25 @@ pq_status pq::finish_iteration(pq_ctx *c, const double *h, double *dmax, bool ti
   std::memcpy(&timeout_flag, &h[4], sizeof timeout_flag);
   if (timeout_flag) {
     c->poisoned = true;
-    return fail(c, PQ_ETIMEOUT, "a tensor-core pipeline wait gave up; the state is invalid");
+    return fail(c, PQ_ETIMEOUT, "a bounded device wait (tensor-core pipeline) gave up; the state is invalid");
   }
+  auto elapsed = [](cudaEvent_t a, cudaEvent_t z) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) {
+      cudaGetLastError();  // leave no error for the next launch check to find
+      ms = 0.f;
+    }
+    return ms;
+  };
   if (timing) {
-    for (int i = 0; i < PQ_NSTEPS - 1; ++i) cudaEventElapsedTime(&c->times[i], c->ev[i], c->ev[i + 1]);
-    cudaEventElapsedTime(&c->times[PQ_NSTEPS - 1], c->ev[0], c->ev[PQ_NSTEPS - 1]);
+    for (int i = 0; i < PQ_NSTEPS - 1; ++i) c->times[i] = elapsed(c->ev[i], c->ev[i + 1]);
+    c->times[PQ_NSTEPS - 1] = elapsed(c->ev[0], c->ev[PQ_NSTEPS - 1]);
     if (!fused) {
       // the passes interleave assembly and products: sum each over the passes
       float t_asm = 0.f, t_bse = 0.f;
       for (int ip = 0; ip < np; ++ip) {
-        float a = 0.f, m = 0.f;
-        cudaEventElapsedTime(&a, c->pev[3 * ip], c->pev[3 * ip + 1]);
-        cudaEventElapsedTime(&m, c->pev[3 * ip + 1], c->pev[3 * ip + 2]);
-        t_asm += a;
-        t_bse += m;
+        t_asm += elapsed(c->pev[3 * ip], c->pev[3 * ip + 1]);
+        t_bse += elapsed(c->pev[3 * ip + 1], c->pev[3 * ip + 2]);
       }
       c->times[5] = t_asm;  // assemble (with chi)
       c->times[7] = t_bse;  // bse
@@ -403,6 +408,9 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.gtab, cs * g.nk * g.n_g},
       {(void **)&b.xph, cs * g.nQ * (size_t)g.n},
       {(void **)&b.xpp, cs * g.nQ * (size_t)g.n},
+      {(void **)&b.gtab32, c->c64 ? sizeof(float2) * g.nk * g.n_g : 0},
+      {(void **)&b.xph32, c->c64 ? sizeof(float2) * g.nQ * (size_t)g.n : 0},
+      {(void **)&b.xpp32, c->c64 ? sizeof(float2) * g.nQ * (size_t)g.n : 0},
       {(void **)&b.k1, cs * 4 * g.nQ},
       {(void **)&b.k2row, cs * 4 * (size_t)g.n * g.nQ},
       {(void **)&b.k2col, cs * 4 * (size_t)g.n * g.nQ},
@@ -422,9 +430,11 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.s2_cph, cs * 2 * g.nQ * (size_t)n_nu},
       {(void **)&b.s2_cpp, cs * g.nQ * (size_t)n_nu},
       {(void **)&b.chi, cs * 4 * g.nQ},
+      {(void **)&b.chi_part, cs * 4 * (size_t)b.q_chunk * g.n_om * ((g.n + 63) / 64)},
       {(void **)&b.gemm_work, cs * 64 * (size_t)g.nk * std::max(z.ntau, g.n_ext)},
   };
   b.gemm_work_elems = 64LL * g.nk * std::max(z.ntau, g.n_ext);
+  b.chi_part_elems = 4LL * b.q_chunk * g.n_om * ((g.n + 63) / 64);
   size_t need = 0;
   for (auto &r : reqs) need += (r.bytes + 255) & ~(size_t)255;
   for (auto &r : reqs) {

@@ -73,9 +73,25 @@ __global__ void gather_kernel(const double *const *scal, int count, const int *e
   if (i == 0) out[5 * count] = (double)*err;
 }
 
+// Elapsed time between two recorded events; 0 (and no error left behind for the next
+// launch check to find) if either was not recorded.
+float elapsed(cudaEvent_t a, cudaEvent_t z) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  return ms;
+}
+
 // Every member's steps, the grouped products with candidate (ti, order), the gather and its copy.
-pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing) {
-  if (timing) BCK(cudaEventRecord(b->ev[0], b->st));
+// In a graph capture the timing events become record nodes of the graph (external records);
+// a plain record during capture would only order work inside the capture.
+pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph = false) {
+  auto rec = [&](cudaEvent_t e) {
+    return in_graph ? cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal) : cudaEventRecord(e, b->st);
+  };
+  if (timing) BCK(rec(b->ev[0]));
   for (pq_ctx *c : b->m) {
     cudaStream_t keep = c->st;
     c->st = b->st;
@@ -83,9 +99,9 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing) {
     c->st = keep;
     if (s != PQ_OK) return bfail(b, s, "member step failed: %s", c->err.c_str());
   }
-  if (timing) BCK(cudaEventRecord(b->ev[1], b->st));
+  if (timing) BCK(rec(b->ev[1]));
   BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->tab[ti][order], (int)b->m.size(), b->tiles[ti], b->err, 0));
-  if (timing) BCK(cudaEventRecord(b->ev[2], b->st));
+  if (timing) BCK(rec(b->ev[2]));
   const int n = (int)b->m.size();
   gather_kernel<<<(n + 127) / 128, 128, 0, b->st>>>(b->scal, n, b->err, b->gather);
   BCK(cudaGetLastError());
@@ -95,7 +111,7 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing) {
 
 pq_status capture(pq_batch *b) {
   BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeRelaxed));
-  pq_status s = enqueue_all(b, b->tile, b->order, b->opt.time_steps != 0);
+  pq_status s = enqueue_all(b, b->tile, b->order, b->opt.time_steps != 0, true);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->st, &g);
   if (s != PQ_OK) {
@@ -231,9 +247,7 @@ pq_status pq_batch_iterate(pq_batch *b, int n_iter, double *max_dsigma) {
       pq_status s = enqueue_all(b, cnd.first, cnd.second, true);
       if (s != PQ_OK) return s;
       BCK(cudaStreamSynchronize(b->st));
-      float ms = 0.f;
-      BCK(cudaEventElapsedTime(&ms, b->ev[1], b->ev[2]));
-      b->tuned[2 * cnd.first + cnd.second] = ms;
+      b->tuned[2 * cnd.first + cnd.second] = elapsed(b->ev[1], b->ev[2]);
       b->cand.erase(b->cand.begin());
       if (b->cand.empty()) {
         int best = -1;
@@ -250,8 +264,8 @@ pq_status pq_batch_iterate(pq_batch *b, int n_iter, double *max_dsigma) {
       BCK(cudaGraphLaunch(b->exec, b->st));
       BCK(cudaStreamSynchronize(b->st));
       if (b->opt.time_steps) {
-        cudaEventElapsedTime(&b->times[0], b->ev[0], b->ev[2]);
-        cudaEventElapsedTime(&b->times[1], b->ev[1], b->ev[2]);
+        b->times[0] = elapsed(b->ev[0], b->ev[2]);
+        b->times[1] = elapsed(b->ev[1], b->ev[2]);
       }
     }
     const double *h = b->host;

@@ -21,6 +21,9 @@ struct Buffers {
   double2 *gtab = nullptr;       // [nk][n_g] G on the table range
   double2 *xph = nullptr;        // [nQ][n] (T/N) G(k) G(k+q)
   double2 *xpp = nullptr;        // [nQ][n] (T/N) G(k) G(q-k)
+  float2 *gtab32 = nullptr;      // FP32 copies of gtab, xph, xpp for the FP32 assembly of the split paths
+  float2 *xph32 = nullptr;
+  float2 *xpp32 = nullptr;
   double2 *k1 = nullptr;         // [4][nQ]
   double2 *k2row = nullptr;      // [4][n][nQ]  (row leg k major, transfer fastest)
   double2 *k2col = nullptr;      // [4][n][nQ]
@@ -43,6 +46,8 @@ struct Buffers {
   double2 *s2_cph = nullptr;     // [2][nQ][n_nu] C-weighted ph tables (d-m, m)
   double2 *s2_cpp = nullptr;     // [nQ][n_nu] C-weighted pp table (s+t)
   double2 *chi = nullptr;        // [4][nQ]
+  double2 *chi_part = nullptr;   // partial sums of chi over row blocks, one pass of slices
+  long long chi_part_elems = 0;
   double2 *gemm_work = nullptr;  // split-K partials of the Sigma~1 transforms
   long long gemm_work_elems = 0;
   // Storage of the BSE operands gam and fv:

@@ -38,13 +38,17 @@ __device__ inline double2 sigma_at(const Grid &g, const double2 *sigma, double c
 }
 
 // Dyson equation G = [G0^-1 - Sigma]^-1 on the table range.
+// G on the table range; gtab32 (split paths) receives the FP32 rounding that their
+// FP32 assembly uses, so it converts nothing per element.
 __global__ void green_kernel(Grid g, const double2 *__restrict__ sigma, const double *__restrict__ scal,
-                             double2 *__restrict__ gtab) {
+                             double2 *__restrict__ gtab, float2 *__restrict__ gtab32) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nk * g.n_g) return;
   int ik = i / g.n_g, n = g.g_lo + i % g.n_g;
   double2 s = sigma_at(g, sigma, scal[0], ik, n);
-  gtab[i] = cinv(g0_inverse(g, ik, n) - s);
+  const double2 v = cinv(g0_inverse(g, ik, n) - s);
+  gtab[i] = v;
+  if (gtab32) gtab32[i] = make_float2((float)v.x, (float)v.y);
 }
 
 __device__ inline double2 gt(const Grid &g, const double2 *gtab, int ik, int n) {
@@ -53,7 +57,7 @@ __device__ inline double2 gt(const Grid &g, const double2 *gtab, int ik, int n) 
 
 // X_ph(Q,k) = (T/N) G(k) G(k+q), X_pp(Q,k) = (T/N) G(k) G(q-k).
 __global__ void bubbles_kernel(Grid g, const double2 *__restrict__ gtab, double2 *__restrict__ xph,
-                               double2 *__restrict__ xpp) {
+                               double2 *__restrict__ xpp, float2 *__restrict__ xph32, float2 *__restrict__ xpp32) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)g.nQ * g.n) return;
   int Q = (int)(i / g.n), k = (int)(i % g.n);
@@ -61,8 +65,14 @@ __global__ void bubbles_kernel(Grid g, const double2 *__restrict__ gtab, double2
   int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
   double c = g.T / g.nk;
   double2 gk = gt(g, gtab, ik, n);
-  xph[i] = c * cmul(gk, gt(g, gtab, kadd(g, ik, iq), n + m));
-  xpp[i] = c * cmul(gk, gt(g, gtab, ksub(g, iq, ik), m - n - 1));
+  const double2 a = c * cmul(gk, gt(g, gtab, kadd(g, ik, iq), n + m));
+  const double2 b = c * cmul(gk, gt(g, gtab, ksub(g, iq, ik), m - n - 1));
+  xph[i] = a;
+  xpp[i] = b;
+  if (xph32) {
+    xph32[i] = make_float2((float)a.x, (float)a.y);
+    xpp32[i] = make_float2((float)b.x, (float)b.y);
+  }
 }
 
 // Tail moments of G = 1/(i nu) + c2/(i nu)^2 + c3/(i nu)^3 + O(nu^-4).
@@ -168,33 +178,49 @@ __device__ inline double2 f_elem(const void *fv, long long ps, long long e) {
   }
 }
 
-// chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k'); one block per (r, Q) of the
-// slices in the operand buffer (nq q-momenta from qb).
+// chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k') for the slices in the operand
+// buffer (nq q-momenta from qb), in two deterministic stages: partial sums over blocks of
+// CHI_ROWS rows (one warp per row at a time, lanes along k'), then their sum per (r, Q).
+constexpr int CHI_ROWS = 64;
+
 template <int FMT>
-__global__ void chi_kernel(Grid g, const void *__restrict__ fv, int ld, int qb, int nq, int q_chunk,
-                           const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
-                           double2 *__restrict__ chi) {
-  __shared__ double2 red[256];
-  const int r = blockIdx.y, Ql = blockIdx.x, Q = qb * g.n_om + Ql;
+__global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, int qb, int nq, int q_chunk,
+                                   const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
+                                   double2 *__restrict__ part) {
+  __shared__ double2 red[8];
+  const int chunk = blockIdx.x, Ql = blockIdx.y, r = blockIdx.z, Q = qb * g.n_om + Ql;
   const long long slabs = (long long)nq * g.n_om;                      // slices per channel in this pass
   const long long ps = 4LL * q_chunk * g.n_om * g.n * (long long)ld;   // plane stride of the buffer
   const double2 *X = (r < 2 ? xph : xpp) + (long long)Q * g.n;
   const long long base = ((long long)r * slabs + Ql) * g.n * (long long)ld;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int k_end = min(g.n, (chunk + 1) * CHI_ROWS);
   double2 acc = make_double2(0.0, 0.0);
-  int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  for (int k = warp; k < g.n; k += nw) {
+  for (int k = chunk * CHI_ROWS + warp; k < k_end; k += 8) {
     double2 rs = make_double2(0.0, 0.0);
     for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem<FMT>(fv, ps, base + (long long)k * ld + kp), X[kp], rs);
-    acc = cfma(X[k], rs, acc);
-    if (lane == 0) acc = acc + X[k];
+    for (int o = 16; o > 0; o >>= 1)
+      rs = make_double2(rs.x + __shfl_xor_sync(0xffffffffu, rs.x, o), rs.y + __shfl_xor_sync(0xffffffffu, rs.y, o));
+    if (lane == 0) acc = acc + cfma(X[k], rs, X[k]);
   }
-  red[threadIdx.x] = acc;
+  if (lane == 0) red[warp] = acc;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = red[0];
+    for (int w = 1; w < 8; ++w) t = t + red[w];
+    part[((long long)r * slabs + Ql) * gridDim.x + chunk] = t;
   }
-  if (threadIdx.x == 0) chi[(long long)r * g.nQ + Q] = make_double2(-red[0].x, -red[0].y);
+}
+
+__global__ void chi_sum_kernel(Grid g, int qb, int nq, int nchunk, const double2 *__restrict__ part,
+                               double2 *__restrict__ chi) {
+  const long long slabs = (long long)nq * g.n_om;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 4 * slabs) return;
+  const int r = (int)(i / slabs), Ql = (int)(i % slabs);
+  double2 t = make_double2(0.0, 0.0);
+  for (int c = 0; c < nchunk; ++c) t = t + part[i * nchunk + c];
+  chi[(long long)r * g.nQ + qb * g.n_om + Ql] = make_double2(-t.x, -t.y);
 }
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -203,12 +229,12 @@ inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b) {
   tail_c1_kernel<<<1, 256, 0, st>>>(g, b.sigma, b.scal);
-  green_kernel<<<nblk((long long)g.nk * g.n_g, 256), 256, 0, st>>>(g, b.sigma, b.scal, b.gtab);
+  green_kernel<<<nblk((long long)g.nk * g.n_g, 256), 256, 0, st>>>(g, b.sigma, b.scal, b.gtab, b.gtab32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b) {
-  bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp);
+  bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp, b.xph32, b.xpp32);
   return cudaGetLastError();
 }
 
@@ -267,13 +293,17 @@ cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b) {
 }
 
 cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int nq) {
-  dim3 grid(nq * g.n_om, 4);
+  const int nchunk = (g.n + CHI_ROWS - 1) / CHI_ROWS;
+  const long long slabs = (long long)nq * g.n_om;
+  if (4 * slabs * nchunk > b.chi_part_elems) return cudaErrorInvalidValue;
+  dim3 grid(nchunk, (unsigned)slabs, 4);
   if (b.vfmt == V_C128)
-    chi_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
+    chi_partial_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
   else if (b.vfmt == V_C64)
-    chi_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
+    chi_partial_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
   else
-    chi_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi);
+    chi_partial_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
+  chi_sum_kernel<<<nblk(4 * slabs, 256), 256, 0, st>>>(g, qb, nq, nchunk, b.chi_part, b.chi);
   return cudaGetLastError();
 }
 

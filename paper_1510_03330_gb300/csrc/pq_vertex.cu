@@ -88,38 +88,67 @@ template <typename C> __device__ inline double2 cdbl(C v);
 template <> __device__ inline double2 cdbl<double2>(double2 v) { return v; }
 template <> __device__ inline double2 cdbl<float2>(float2 v) { return make_double2(v.x, v.y); }
 
-// BF16 operand planes of the split BSE: x = h + l (+ r for F), each piece the
-// BF16 rounding of what the previous pieces leave (the differences are exact in FP32).
-__device__ inline void store_planes2(__nv_bfloat16 *p, long long ps, long long o, float2 v) {
-  const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-  p[o] = rh;
-  p[ps + o] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
-  p[2 * ps + o] = ih;
-  p[3 * ps + o] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+// BF16 rounding (to nearest, ties to even) of finite FP32 values in integer arithmetic:
+// the upper half of u + 0x7FFF + (bit 16 of u).  Identical to the hardware conversion,
+// but it runs on the integer ALU instead of the conversion unit, which is narrow on this
+// part and otherwise bounds the assembly.
+__device__ inline uint32_t bf16_round(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return u + 0x7FFFu + ((u >> 16) & 1u);
 }
-__device__ inline void store_planes3(__nv_bfloat16 *p, long long ps, long long o, float2 v) {
-  const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-  const float rr = v.x - __bfloat162float(rh), ir = v.y - __bfloat162float(ih);
-  const __nv_bfloat16 rl = __float2bfloat16_rn(rr), il = __float2bfloat16_rn(ir);
-  p[o] = rh;
-  p[ps + o] = ih;
-  p[2 * ps + o] = rl;
-  p[3 * ps + o] = il;
-  p[4 * ps + o] = __float2bfloat16_rn(rr - __bfloat162float(rl));
-  p[5 * ps + o] = __float2bfloat16_rn(ir - __bfloat162float(il));
+// (k', k'+1) values -> packed BF16 pair (k' in the low half) and the FP32 remainders
+__device__ inline uint32_t split_pair(float x0, float x1, float &r0, float &r1) {
+  const uint32_t a = bf16_round(x0), b = bf16_round(x1);
+  r0 = x0 - __uint_as_float(a & 0xFFFF0000u);
+  r1 = x1 - __uint_as_float(b & 0xFFFF0000u);
+  return __byte_perm(a, b, 0x7632);
+}
+__device__ inline uint32_t pack_pair(float x0, float x1) {
+  return __byte_perm(bf16_round(x0), bf16_round(x1), 0x7632);
 }
 
+// Output of the BSE operands.  Lanes 2j and 2j+1 of a warp always hold consecutive
+// columns k', k'+1 of one row (Nnu is even and the element index has the lane's parity),
+// so each pair shares its stores: one shuffle gives the even lane both elements' real
+// parts and the odd lane both imaginary parts, and each writes its half as 4-byte BF16
+// pairs (split planes), or, for complex64, the even lane writes the pair's Gamma X and
+// the odd lane its F as 16-byte stores.
+//
+// BF16 planes: x = h + l (+ r for F), each piece the BF16 rounding of what the previous
+// pieces leave (the differences are exact in FP32).  Plane order: Gamma X (Re h, Re l,
+// Im h, Im l), F (Re h, Im h, Re l, Im l, Re r, Im r).
 template <typename S, bool PL>
 struct Out {
   void *gam, *fv;
-  long long ps;  // plane stride (PL)
+  long long ps;  // plane stride in elements (PL)
+  // element o of this lane (o is even on even lanes, odd on odd lanes)
   __device__ inline void put(long long o, float2 ga, float2 f) const {
+    const unsigned mask = __activemask();
+    const bool odd = threadIdx.x & 1;
+    // even lanes send Im, odd lanes send Re: each receives the partner's half it stores
+    const float ga_in = __shfl_xor_sync(mask, odd ? ga.x : ga.y, 1);
+    const float f_in = __shfl_xor_sync(mask, odd ? f.x : f.y, 1);
+    const long long o2 = o >> 1;  // the pair's index in BF16x2 units
     if constexpr (PL) {
-      store_planes2((__nv_bfloat16 *)gam, ps, o, ga);
-      store_planes3((__nv_bfloat16 *)fv, ps, o, f);
+      uint32_t *pg = (uint32_t *)gam, *pf = (uint32_t *)fv;
+      const long long ps2 = ps >> 1;
+      // (element k', element k'+1) of this lane's part
+      const float g0 = odd ? ga_in : ga.x, g1 = odd ? ga.y : ga_in;
+      const float f0 = odd ? f_in : f.x, f1 = odd ? f.y : f_in;
+      const int part = odd ? 1 : 0;
+      float r0, r1, s0, s1;
+      pg[(2 * part) * ps2 + o2] = split_pair(g0, g1, r0, r1);
+      pg[(2 * part + 1) * ps2 + o2] = pack_pair(r0, r1);
+      pf[part * ps2 + o2] = split_pair(f0, f1, r0, r1);
+      pf[(2 + part) * ps2 + o2] = split_pair(r0, r1, s0, s1);
+      pf[(4 + part) * ps2 + o2] = pack_pair(s0, s1);
     } else {
-      ((S *)gam)[o] = ga;
-      ((S *)fv)[o] = f;
+      // complex64: the even lane needs the odd lane's Gamma X, the odd lane the even lane's F
+      const float ga_y = __shfl_xor_sync(mask, ga.y, 1), f_x = __shfl_xor_sync(mask, f.x, 1);
+      if (!odd)
+        *reinterpret_cast<float4 *>((S *)gam + 2 * o2) = make_float4(ga.x, ga.y, ga_in, ga_y);
+      else
+        *reinterpret_cast<float4 *>((S *)fv + 2 * o2) = make_float4(f_x, f_in, f.x, f.y);
     }
   }
   __device__ inline void put(long long o, double2 ga, double2 f) const {
@@ -135,12 +164,11 @@ struct Out {
 // momenta) writes the d/m outputs at q and the s/t outputs at q' = k + k' + q of one gather
 // step; otherwise each target momentum takes two gather steps, one per channel pair.
 template <typename S, typename C, bool PL>
-__global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restrict__ phi, Out<S, PL> out, int ld,
+__global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__restrict__ phi, Out<S, PL> out, int ld,
                                                        const double2 *__restrict__ k1,
                                                        const double2 *__restrict__ k2row,
-                                                       const double2 *__restrict__ xph,
-                                                       const double2 *__restrict__ xpp,
-                                                       const double2 *__restrict__ gtab, double2 *__restrict__ dfpart,
+                                                       const C *__restrict__ xph, const C *__restrict__ xpp,
+                                                       const C *__restrict__ gtab, double2 *__restrict__ dfpart,
                                                        Lam lam, Pass pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.n_om * g.n_nu;
@@ -163,7 +191,9 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
   const long long chan = (long long)g.nQ * nn * nn;                        // channel stride of Phi
   const long long ochan = (long long)pass.nq * g.n_om * nn * ld;            // channel stride of the outputs
   const int tmom = ksub(g, ikp, ik);
-  const double2 *xph_ = xph, *xpp_ = xpp;
+  const C *xph_ = xph, *xpp_ = xpp;
+  // exact e / Nnu for e < 2^16 by multiply-high with ceil(2^32 / Nnu) (Nnu >= 2)
+  const unsigned nnu_magic = 0xFFFFFFFFu / (unsigned)g.n_nu + 1u;
 
   for (int t = threadIdx.x; t < 2 * g.n_om; t += blockDim.x) {
     int x = t / g.n_om, mt = t % g.n_om;
@@ -201,7 +231,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
     }
     __syncthreads();
     for (int e = threadIdx.x; e < NB; e += blockDim.x) {
-      const int mi = e / g.n_nu, npi = e % g.n_nu;
+      const int mi = (int)__umulhi((unsigned)e, nnu_magic), npi = e - mi * g.n_nu;
       const int m = g.m_lo + mi, np_ = g.n_lo + npi;
       const int mt = np_ - n;  // transfer k' - k of maps A and C
       const bool inT = (mt >= g.m_lo && mt <= g.m_hi);
@@ -231,11 +261,11 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const C Fd = Gd + od, Fm = Gm + om;
       const int Q = iq * g.n_om + mi;
       const long long o_dm = ((long long)(Q - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
-      const C xq = cfrom<C>(xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
+      const C xq = (xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
       out.put(o_dm, cmul(Gd, xq), Fd);
       out.put(ochan + o_dm, cmul(Gm, xq), Fm);
       // Eq. PA_Sigma, ph part: G(k+q) X_ph(Q,k') [F_d - F_m - (Lambda0_d - Lambda0_m)]
-      const C gkq = cfrom<C>(gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
+      const C gkq = (gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
       acc = cfma(cmul(gkq, xq), Fd - Fm - twoU, acc);
       }
       if (do_st) {
@@ -263,11 +293,11 @@ __global__ void __launch_bounds__(256) assemble_kernel(Grid g, const S *__restri
       const C Fs = Gs + os, Ft = Gt + ot;
       const int Qp = iqp * g.n_om + mi;
       const long long o_st = ((long long)(Qp - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
-      const C xqp = cfrom<C>(xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
+      const C xqp = (xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
       out.put(2 * ochan + o_st, (-0.5f) * cmul(Gs, xqp), Fs);
       out.put(3 * ochan + o_st, 0.5f * cmul(Gt, xqp), Ft);
       // pp part: G(q'-k) X_pp(Q',k') [F_s + F_t - (Lambda0_s + Lambda0_t)]
-      const C gqk = cfrom<C>(gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
+      const C gqk = (gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
       acc = cfma(cmul(gqk, xqp), Fs + Ft - twoU, acc);
       }
     }
@@ -310,8 +340,19 @@ static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, L
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   Out<S, PL> out{b.gam, b.fv, ps};
-  kfn<<<dim3(g.nk, g.n), 256, sm, st>>>(g, (const S *)b.phi, out, b.ld, b.k1, b.k2row, b.xph, b.xpp, b.gtab,
-                                        b.dfpart, lam, p);
+  // the FP32 assembly reads FP32 copies of the one-particle tables (no conversion per element)
+  const C *xph, *xpp, *gtab;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    xph = (const C *)b.xph32;
+    xpp = (const C *)b.xpp32;
+    gtab = (const C *)b.gtab32;
+  } else {
+    xph = (const C *)b.xph;
+    xpp = (const C *)b.xpp;
+    gtab = (const C *)b.gtab;
+  }
+  kfn<<<dim3(g.nk, g.n), 256, sm, st>>>(g, (const S *)b.phi, out, b.ld, b.k1, b.k2row, xph, xpp, gtab, b.dfpart, lam,
+                                        p);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,9 @@ CONFIGS = {
     "square8_u2_b4": Params(SQUARE, beta=4.0, U=2.0, mu=0.0, L=8, n_nu=16, n_Omega=16),
     # large single solve: 8x8 momenta, 24 frequencies: BSE matrices of 1536 x 1536
     "square8_u3_b8_nu24": Params(SQUARE, beta=8.0, U=3.0, mu=0.0, L=8, n_nu=24, n_Omega=24),
+    # the large solve's frequency box on the 4x4 lattice (n = 384, 0.45 GB of Phi): a small
+    # case of the same kernels for profiling captures
+    "square4_u3_b8_nu24": Params(SQUARE, beta=8.0, U=3.0, mu=0.0, L=4, n_nu=24, n_Omega=24),
 }
 
 
