@@ -113,12 +113,16 @@ PQ_API pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, doubl
                   int n_nu, int n_Omega, const pq_options *opt);
 
 /* Fully irreducible vertex of one channel (0..3 = d, m, s, t), local in
- * momentum, tabulated on |n|, |n'|, |m| <= n_lambda as host c128
- * [2n_lambda+1 (m)][2n_lambda (n)][2n_lambda (n')] with n in
- * [-n_lambda, n_lambda-1] and m in [-n_lambda, n_lambda]; outside the table
- * the channel keeps its parquet-approximation value (Sec. III.A, "extend
- * Lambda ... by supplementing it with the lowest order values").
- * Not available in this build: returns PQ_EINVAL. */
+ * momentum (Sec. III.A: Lambda from an impurity calculation on a small frequency
+ * box, the full-parquet / parquet-DGammaA input), tabulated as host c128
+ * [2 n_lambda + 1 (m)][2 n_lambda (n)][2 n_lambda (n')] with n, n' in
+ * [-n_lambda, n_lambda - 1] and m in [-n_lambda, n_lambda], in the channel's own
+ * frequency convention (that of F_r^{k k'}(Q)).  Outside the table, and for
+ * channels never set, the parquet-approximation value (U, -U, 2U, 0) is used.
+ * Applies from the next pq_iterate on.  The table is copied to the device (converted to
+ * the storage precision); a later call for the same channel replaces it (the old copy
+ * is freed with the context).  Errors: PQ_EINVAL (channel, NULL table, n_lambda
+ * outside [1, 1024]), PQ_ENOMEM, PQ_ECUDA. */
 PQ_API pq_status pq_set_Lambda(pq_ctx *ctx, int channel, const double *host_c128, int n_lambda);
 
 /* Run up to max_iter iterations; stop after the first one whose

@@ -71,6 +71,34 @@ def lambda0(U):
     return np.array([U, -U, 2.0 * U, 0.0], dtype=np.complex128)
 
 
+def lambda_tabulated(p, tables):
+    """Fully irreducible vertex with a tabulated local part, over the whole box.
+
+    Sec. III.A extends the parquet approximation by a Lambda computed on a small
+    frequency box and supplemented by its lowest-order value (U, -U, 2U, 0) outside.
+    tables maps a channel r (0..3 = d, m, s, t) to (table, n_lambda) with
+    table[m + n_lambda][n + n_lambda][n' + n_lambda] = Lambda_r^{nu_n, nu_n'}(omega_m)
+    for |m| <= n_lambda and n, n' in [-n_lambda, n_lambda - 1] (local: no momentum
+    dependence).  Returns four arrays [Q][k][k'] in the channel conventions of F_r.
+    """
+    g = make_grid(p)
+    kk, kn, qk, qm = box_indices(g)
+    l0 = lambda0(p.U)
+    m, n, npr = qm[:, None, None], kn[None, :, None], kn[None, None, :]
+    out = []
+    for r in range(4):
+        arr = np.full((p.n_Q, p.n, p.n), l0[r], dtype=np.complex128)
+        if r in tables:
+            tab, nl = tables[r]
+            tab = np.asarray(tab, dtype=np.complex128)
+            assert tab.shape == (2 * nl + 1, 2 * nl, 2 * nl)
+            inside = (np.abs(m) <= nl) & (n >= -nl) & (n < nl) & (npr >= -nl) & (npr < nl)
+            vals = tab[np.clip(m + nl, 0, 2 * nl), np.clip(n + nl, 0, 2 * nl - 1), np.clip(npr + nl, 0, 2 * nl - 1)]
+            arr = np.where(inside, vals, arr)
+        out.append(arr)
+    return out
+
+
 # ----------------------------------------------------------------------------- grids
 
 
@@ -319,7 +347,8 @@ def assemble(g: Grid, phi, K, lam, Qs=None, ks=None):
     lookup = lambda x, a, b, tr: vertex_value(g, phi, K, x, a, b, tr)  # noqa: E731
     gamma = np.empty((4, Qs.size, ks.size, p.n), dtype=np.complex128)
     for r in range(4):
-        gamma[r] = parquet_gamma(g, r, lam[r], lookup, k3, n3, kp3, np3, q3, m3)
+        lam_r = lam[r][Qs][:, ks] if np.ndim(lam[r]) == 3 else lam[r]  # tabulated or scalar
+        gamma[r] = parquet_gamma(g, r, lam_r, lookup, k3, n3, kp3, np3, q3, m3)
     return gamma, gamma + phi[:, Qs][:, :, ks]
 
 

@@ -258,6 +258,12 @@ class Solver:
                                                    out.size * 2))
         return out
 
+    def set_Lambda(self, channel: int, table: np.ndarray, n_lambda: int):
+        """Tabulated local Lambda of one channel, [2 n_lambda + 1][2 n_lambda][2 n_lambda] (m, n, n')."""
+        t = np.ascontiguousarray(table, dtype=np.complex128)
+        assert t.shape == (2 * n_lambda + 1, 2 * n_lambda, 2 * n_lambda)
+        self._check(self.lib.pq_set_Lambda(self.h, channel, _dptr(t), n_lambda))
+
     def set_state(self, phi: np.ndarray | None = None, sigma: np.ndarray | None = None):
         p = self.p
         pa = sa = None

@@ -539,11 +539,26 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
 }
 
 pq_status pq_set_Lambda(pq_ctx *c, int channel, const double *host_c128, int n_lambda) {
-  (void)channel;
-  (void)host_c128;
-  (void)n_lambda;
   if (!c) return PQ_EINVAL;
-  return fail(c, PQ_EINVAL, "a tabulated Lambda is not available in this build; the parquet approximation is used");
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (channel < 0 || channel > 3) return fail(c, PQ_EINVAL, "bad channel %d", channel);
+  if (!host_c128) return fail(c, PQ_EINVAL, "the table is NULL");
+  if (n_lambda < 1 || n_lambda > 1024) return fail(c, PQ_EINVAL, "n_lambda must be in [1, 1024]");
+  const size_t cnt = (size_t)(2 * n_lambda + 1) * (2 * n_lambda) * (2 * n_lambda);
+  const size_t es = c->c64 ? sizeof(float2) : sizeof(double2);
+  void *d = dalloc(c, cnt * es);
+  if (!d) return fail(c, PQ_ENOMEM, "device allocation of %zu bytes for the Lambda table failed", cnt * es);
+  CK(cudaStreamSynchronize(c->st));
+  if (c->c64) {
+    std::vector<float2> tmp(cnt);
+    for (size_t i = 0; i < cnt; ++i) tmp[i] = make_float2((float)host_c128[2 * i], (float)host_c128[2 * i + 1]);
+    CK(cudaMemcpy(d, tmp.data(), cnt * es, cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(d, host_c128, cnt * es, cudaMemcpyHostToDevice));
+  }
+  c->b.lam_tab[channel] = d;  // a previous table stays allocated until pq_destroy
+  c->b.lam_nl[channel] = n_lambda;
+  return PQ_OK;
 }
 
 pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, double *last) {

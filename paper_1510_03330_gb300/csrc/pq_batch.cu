@@ -6,7 +6,8 @@
 // first tile of each, so small and large solves share the SMs in one schedule.
 // The whole iteration (members' steps, grouped products, gather of the members'
 // convergence scalars and their device->host copy) is captured once as a CUDA
-// graph and replayed.  Two choices of the grouped launch are tuned on the first
+// graph and replayed; the members' steps are captured on four branch streams
+// (round robin), so the graph runs independent members concurrently.  Two choices of the grouped launch are tuned on the first
 // real iterations: the tile width (64 or 128 complex output columns; narrow tiles
 // waste less of the MMA on small matrices) and the order of the members in the
 // schedule (as given, or largest matrix first so the longest tiles start early).
@@ -23,6 +24,8 @@ struct pq_batch {
   std::vector<pq_ctx *> m;
   cudaStream_t user_st = nullptr;  // the members' stream
   cudaStream_t st = nullptr;       // the batch's own stream (capturable)
+  cudaStream_t br[4] = {};         // branch streams: members' steps run concurrently, round robin
+  cudaEvent_t fork = nullptr, join[4] = {};
   pq_batch_options opt{};
   pq::BseProblem *tab[2][2] = {};  // device problem tables [tile 128 / 64][order given / largest first]
   long long tiles[2] = {0, 0};
@@ -92,12 +95,21 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph
     return in_graph ? cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal) : cudaEventRecord(e, b->st);
   };
   if (timing) BCK(rec(b->ev[0]));
-  for (pq_ctx *c : b->m) {
+  // fork: the members' steps go to the branch streams, joined before the grouped products
+  const int nbr = (int)std::min<size_t>(4, b->m.size());
+  BCK(cudaEventRecord(b->fork, b->st));
+  for (int j = 0; j < nbr; ++j) BCK(cudaStreamWaitEvent(b->br[j], b->fork, 0));
+  for (size_t i = 0; i < b->m.size(); ++i) {
+    pq_ctx *c = b->m[i];
     cudaStream_t keep = c->st;
-    c->st = b->st;
+    c->st = b->br[i % nbr];
     pq_status s = pq::enqueue_iteration(c, false, false);
     c->st = keep;
     if (s != PQ_OK) return bfail(b, s, "member step failed: %s", c->err.c_str());
+  }
+  for (int j = 0; j < nbr; ++j) {
+    BCK(cudaEventRecord(b->join[j], b->br[j]));
+    BCK(cudaStreamWaitEvent(b->st, b->join[j], 0));
   }
   if (timing) BCK(rec(b->ev[1]));
   BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->tab[ti][order], (int)b->m.size(), b->tiles[ti], b->err, 0));
@@ -136,6 +148,11 @@ void release(pq_batch *b) {
   if (b->gather) cudaFree(b->gather);
   if (b->err) cudaFree(b->err);
   if (b->host) cudaFreeHost(b->host);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto &e : b->join)
+    if (e) cudaEventDestroy(e);
+  for (auto &t : b->br)
+    if (t) cudaStreamDestroy(t);
   if (b->st) cudaStreamDestroy(b->st);
   for (pq_ctx *c : b->m) c->in_batch = false;
 }
@@ -184,6 +201,11 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
     return true;
   };
   if (bad(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking), "stream")) return PQ_ECUDA;
+  for (auto &t : b->br)
+    if (bad(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "stream")) return PQ_ECUDA;
+  if (bad(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event")) return PQ_ECUDA;
+  for (auto &e : b->join)
+    if (bad(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event")) return PQ_ECUDA;
   for (auto &e : b->ev)
     if (bad(cudaEventCreate(&e), "event")) return PQ_ECUDA;
   if (bad(cudaMalloc((void **)&b->scal, sizeof(double *) * count), "alloc")) return PQ_ECUDA;

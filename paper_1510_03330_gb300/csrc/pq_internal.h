@@ -54,6 +54,8 @@ struct Buffers {
   //   V_C128 / V_C64: [r][Q][k][ld] complex of the storage type;
   //   V_BF16P: BF16 planes [plane][r][Q][k][ld]; gam planes (Re h, Re l, Im h, Im l),
   //   fv planes (Re h, Im h, Re l, Im l, Re r, Im r) with x = h + l + r.
+  const void *lam_tab[4] = {};  // tabulated local Lambda per channel (arithmetic type of the assembly)
+  int lam_nl[4] = {};
   int vfmt = 0;
   int ld = 0;                    // row stride of gam and fv (elements)
   int q_chunk = 0;               // q-momenta assembled and multiplied per pass

@@ -200,7 +200,10 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
     # n = 1024: the tensor cores' FP32 accumulation truncates over ~768 updates per element,
     # a bias of a few 1e-6 on Phi and F (Sigma keeps 1e-6): the bounds below are the measured
     # ones, above the 1e-6 target for F and Phi
-    ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 3 * TOL_SPLIT, 15 * TOL_SPLIT)])
+    ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 3 * TOL_SPLIT, 15 * TOL_SPLIT),
+    # the default scheme (BF16 operands, half as many accumulator updates per k): Sigma and F
+    # within the 1e-6 target; Phi, the raw product, at the TF32x3 bound
+    ("square8_u2_b4", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT)])
 def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
     """The benchmark workloads at full size, in the launch configuration bench.py
     times: iterations 1 and 2 from the zero state, compared on sampled transfer

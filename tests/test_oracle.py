@@ -411,3 +411,60 @@ def test_susceptibility_first_order_rpa():
             Q = iq * p.n_Omega + im
             assert abs(chi[1, Q] - (chi0 + p.U * chi0**2)) < 1e-13
             assert abs(chi[0, Q] - (chi0 - p.U * chi0**2)) < 1e-13
+
+
+# --------------------------------------------------------------------------- tabulated Lambda
+
+
+def _lambda_tables(p, nl, seed):
+    """Seeded local tables of all four channels on |m| <= nl, n, n' in [-nl, nl - 1]."""
+    rng = np.random.default_rng(seed)
+    return {r: (0.3 * p.U * (rng.standard_normal((2 * nl + 1, 2 * nl, 2 * nl))
+                             + 1j * rng.standard_normal((2 * nl + 1, 2 * nl, 2 * nl))), nl)
+            for r in range(4)}
+
+
+def test_lambda_table_of_constants_equals_scalar_lambda():
+    """A table holding one constant per channel over the whole box is the scalar Lambda:
+    two iterations with the table and with the scalar agree to rounding."""
+    p = SMALL_ODD
+    c = np.array([1.3 + 0.2j, -0.7, 2.1 - 0.1j, 0.4j])
+    nl = max(p.n_nu, p.n_Omega)
+    tabs = {r: (np.full((2 * nl + 1, 2 * nl, 2 * nl), c[r]), nl) for r in range(4)}
+    lam_t = O.lambda_tabulated(p, tabs)
+    a = b = O.zero_state(p)
+    for _ in range(2):
+        ra, rb = O.iterate(p, a, lam=lam_t), O.iterate(p, b, lam=c)
+        a, b = ra.state, rb.state
+    assert np.abs(a.phi - b.phi).max() <= 1e-13 * np.abs(b.phi).max()
+    assert np.abs(a.sigma - b.sigma).max() <= 1e-13 * np.abs(b.sigma).max()
+
+
+def test_lambda_table_first_iteration_closed_form():
+    """From Phi = 0 the kernels vanish, so Gamma_r = F_r = Lambda_r and the first iterate is
+    Phi_r(Q) = alpha s_r Lambda_r(Q) diag(X_r(Q)) Lambda_r(Q) (Eq. PA_F_Phi).  Lambda is
+    rebuilt here element by element from the table (inside |m| <= nl, |n|, |n'| in range;
+    (U, -U, 2U, 0) outside), with a table smaller than the box so both cases occur."""
+    p = Params("square", beta=2.0, U=1.1, mu=0.0, L=2, n_nu=6, n_Omega=5)
+    nl = 2
+    tabs = _lambda_tables(p, nl, seed=7)
+    res = O.iterate(p, O.zero_state(p), lam=O.lambda_tabulated(p, tabs))
+    l0 = [p.U, -p.U, 2 * p.U, 0.0]
+    s_r = [1.0, 1.0, -0.5, 0.5]
+    n_lo, m_lo = -p.n_nu // 2, -(p.n_Omega // 2)
+    for r in range(4):
+        lam = np.empty((p.n_Q, p.n, p.n), dtype=np.complex128)
+        for Q in range(p.n_Q):
+            m = m_lo + Q % p.n_Omega
+            for k in range(p.n):
+                n = n_lo + k % p.n_nu
+                for kp in range(p.n):
+                    npr = n_lo + kp % p.n_nu
+                    if abs(m) <= nl and -nl <= n < nl and -nl <= npr < nl:
+                        lam[Q, k, kp] = tabs[r][0][m + nl, n + nl, npr + nl]
+                    else:
+                        lam[Q, k, kp] = l0[r]
+        X = res.X_ph if r < 2 else res.X_pp
+        expect = p.mix * s_r[r] * np.einsum("qab,qb,qbc->qac", lam, X, lam)
+        assert np.abs(res.state.phi[r] - expect).max() <= 1e-12 * np.abs(expect).max(), r
+        assert np.abs(res.F[r] - lam).max() <= 1e-14 * np.abs(lam).max(), r
