@@ -194,6 +194,22 @@ def blas_threads():
 # ----------------------------------------------------------------------------- main
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, elapsed_s):
+    """Whole-job throughput of N replica ranks: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / elapsed_s
+
+
 BATCH = "batch64_seed1510"
 
 
@@ -348,18 +364,14 @@ def main():
 
     if a.workload == BATCH:
         r = run_batch(a, world, barrier, lambda: ClockSampler(local))
-        ms = r["batch_ms"]
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(r["batch_ms"], dist, "cuda")
         pk, src = peaks()
         bse_tflops = r["flops_per_iter"] * a.steps / (r["bse_ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": bse_tflops, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": bse_tflops / pk["bf16_tflops"], "traffic": None, "kernel": "bse (grouped)",
                 "executed_tensor_frac": 3.0 * bse_tflops / pk["bf16_tflops"],
                 "peak_source": f"{src} bf16 burst"}
-        line = {"metric": METRIC, "value": world * a.steps / (ms / 1e3), "unit": "batch iter/s (64 solves)",
+        line = {"metric": METRIC, "value": job_rate(a.steps, world, ms / 1e3), "unit": "batch iter/s (64 solves)",
                 "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[SPLIT_BF16X3],
                 "data": "synthetic", "config": dict(cfg, waves=r["waves"]), "roofline": roof,
@@ -425,12 +437,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    value = job_rate(a.steps, world, ms / 1e3)
     dev_bytes = solver.device_bytes
     solver.close()
     del solver
@@ -521,13 +529,10 @@ def main():
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         s.close()
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, "cuda")
         M, ntau = p.tau_matsubara, p.tau_panels * p.tau_order
         h2d = 16 * (2 * M * ntau + ntau * p.n_ext + 2 * p.n_k**2) + 8 * ntau
-        line["e2e"] = {"value": world * a.steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
+        line["e2e"] = {"value": job_rate(a.steps, world, el), "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
                        "d2h_bytes_per_step": sig.nbytes + chi.nbytes / a.steps,
                        "note": "includes context set-up and the upload of the imaginary-time transform tables"}
 

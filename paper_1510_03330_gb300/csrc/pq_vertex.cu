@@ -86,11 +86,14 @@ struct Lam {
   int nl[4];
 };
 
-template <typename C>
+// Lambda_r at (m, n, n'); without tables (TAB false) the constant, at no cost.
+template <bool TAB, typename C>
 __device__ inline C lam_at(const Lam &lam, int r, C l_r, int m, int n, int np_) {
-  const int nl = lam.nl[r];
-  if (lam.tab[r] && m >= -nl && m <= nl && n >= -nl && n < nl && np_ >= -nl && np_ < nl)
-    return ((const C *)lam.tab[r])[((m + nl) * 2 * nl + (n + nl)) * 2 * nl + (np_ + nl)];
+  if constexpr (TAB) {
+    const int nl = lam.nl[r];
+    if (lam.tab[r] && m >= -nl && m <= nl && n >= -nl && n < nl && np_ >= -nl && np_ < nl)
+      return ((const C *)lam.tab[r])[((m + nl) * 2 * nl + (n + nl)) * 2 * nl + (np_ + nl)];
+  }
   return l_r;
 }
 
@@ -137,53 +140,39 @@ template <typename S, bool PL>
 struct Out {
   void *gam, *fv;
   long long ps;  // plane stride in elements (PL)
-};
-
-// The writer of one thread.  Outputs are addressed by pair index o2 (element index of
-// the pair's first column k' over two); the plane bases of this lane's half are formed
-// once, so a store costs one 64-bit add and no 64-bit multiply.
-template <typename S, bool PL>
-struct Writer {
-  uint32_t *g0, *f0;  // PL: this lane's first Gamma X plane and first F plane (BF16 pairs)
-  long long ps2;      // PL: plane stride in BF16 pairs
-  S *gam, *fv;
-  bool odd;
-  __device__ explicit Writer(const Out<S, PL> &o) {
-    odd = threadIdx.x & 1;
-    ps2 = o.ps >> 1;
-    gam = (S *)o.gam;
-    fv = (S *)o.fv;
-    g0 = (uint32_t *)o.gam + (odd ? 2 * ps2 : 0);  // Re h, Re l | Im h, Im l
-    f0 = (uint32_t *)o.fv + (odd ? ps2 : 0);       // Re h, Im h, Re l, Im l, Re r, Im r
-  }
-  __device__ inline void put(long long o2, float2 ga, float2 f) const {
+  // element o of this lane (o is even on even lanes, odd on odd lanes)
+  __device__ inline void put(long long o, float2 ga, float2 f) const {
     const unsigned mask = __activemask();
+    const bool odd = threadIdx.x & 1;
     // even lanes send Im, odd lanes send Re: each receives the partner's half it stores
     const float ga_in = __shfl_xor_sync(mask, odd ? ga.x : ga.y, 1);
     const float f_in = __shfl_xor_sync(mask, odd ? f.x : f.y, 1);
+    const long long o2 = o >> 1;  // the pair's index in BF16x2 units
     if constexpr (PL) {
+      uint32_t *pg = (uint32_t *)gam, *pf = (uint32_t *)fv;
+      const long long ps2 = ps >> 1;
       // (element k', element k'+1) of this lane's part
-      const float gv0 = odd ? ga_in : ga.x, gv1 = odd ? ga.y : ga_in;
-      const float fv0 = odd ? f_in : f.x, fv1 = odd ? f.y : f_in;
+      const float g0 = odd ? ga_in : ga.x, g1 = odd ? ga.y : ga_in;
+      const float f0 = odd ? f_in : f.x, f1 = odd ? f.y : f_in;
+      const int part = odd ? 1 : 0;
       float r0, r1, s0, s1;
-      uint32_t *pg = g0 + o2, *pf = f0 + o2;
-      pg[0] = split_pair(gv0, gv1, r0, r1);
-      pg[ps2] = pack_pair(r0, r1);
-      pf[0] = split_pair(fv0, fv1, r0, r1);
-      pf[2 * ps2] = split_pair(r0, r1, s0, s1);
-      pf[4 * ps2] = pack_pair(s0, s1);
+      pg[(2 * part) * ps2 + o2] = split_pair(g0, g1, r0, r1);
+      pg[(2 * part + 1) * ps2 + o2] = pack_pair(r0, r1);
+      pf[part * ps2 + o2] = split_pair(f0, f1, r0, r1);
+      pf[(2 + part) * ps2 + o2] = split_pair(r0, r1, s0, s1);
+      pf[(4 + part) * ps2 + o2] = pack_pair(s0, s1);
     } else {
       // complex64: the even lane needs the odd lane's Gamma X, the odd lane the even lane's F
       const float ga_y = __shfl_xor_sync(mask, ga.y, 1), f_x = __shfl_xor_sync(mask, f.x, 1);
       if (!odd)
-        *reinterpret_cast<float4 *>(gam + 2 * o2) = make_float4(ga.x, ga.y, ga_in, ga_y);
+        *reinterpret_cast<float4 *>((S *)gam + 2 * o2) = make_float4(ga.x, ga.y, ga_in, ga_y);
       else
-        *reinterpret_cast<float4 *>(fv + 2 * o2) = make_float4(f_x, f_in, f.x, f.y);
+        *reinterpret_cast<float4 *>((S *)fv + 2 * o2) = make_float4(f_x, f_in, f.x, f.y);
     }
   }
-  __device__ inline void put(long long o2, double2 ga, double2 f) const {
-    gam[2 * o2 + odd] = ga;
-    fv[2 * o2 + odd] = f;
+  __device__ inline void put(long long o, double2 ga, double2 f) const {
+    ((S *)gam)[o] = ga;
+    ((S *)fv)[o] = f;
   }
 };
 
@@ -193,7 +182,7 @@ struct Writer {
 // buffers hold their 4 * nq * NOmega slices with rows of ld elements.  A fused pass (all
 // momenta) writes the d/m outputs at q and the s/t outputs at q' = k + k' + q of one gather
 // step; otherwise each target momentum takes two gather steps, one per channel pair.
-template <typename S, typename C, bool PL>
+template <typename S, typename C, bool PL, bool TAB>
 __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__restrict__ phi, Out<S, PL> out, int ld,
                                                        const double2 *__restrict__ k1,
                                                        const double2 *__restrict__ k2row,
@@ -222,10 +211,6 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
   const long long ochan = (long long)pass.nq * g.n_om * nn * ld;            // channel stride of the outputs
   const int tmom = ksub(g, ikp, ik);
   const C *xph_ = xph, *xpp_ = xpp;
-  const Writer<S, PL> wr(out);
-  const long long ochan2 = ochan >> 1;           // output channel stride in pairs
-  const int slab = g.n * g.n;                     // Phi slice size (elements)
-  const int half_oslab = (int)((long long)g.n * ld / 2);  // output slice size in pairs
   // exact e / Nnu for e < 2^16 by multiply-high with ceil(2^32 / Nnu) (Nnu >= 2)
   const unsigned nnu_magic = 0xFFFFFFFFu / (unsigned)g.n_nu + 1u;
 
@@ -250,29 +235,22 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
     const int iqp = kadd(g, kadd(g, ik, ikp), iq);
     const int cmom = kadd(g, ik, iq);
     const int pqk = ksub(g, iqp, ik);  // momentum of q' - k
-    // 64-bit bases of this step; per element only 32-bit offsets (mt, mi times a slab)
-    const S *phR = phi + ((long long)(tmom * g.n_om) * nn + k) * nn + cmom * g.n_nu;
-    const S *phP = phi + ((long long)(iq * g.n_om) * nn + k) * nn + ikp * g.n_nu;
-    const S *phS = phi + 2 * chan + ((long long)(iqp * g.n_om) * nn + k) * nn + ikp * g.n_nu;
     __syncthreads();
     for (int e = threadIdx.x; e < NB; e += blockDim.x) {
-      const int mt = (int)__umulhi((unsigned)e, nnu_magic), c = e - mt * g.n_nu;
-      const int off = mt * slab + c;
-      Rd[mt * RS + c] = phR[off];
-      Rm[mt * RS + c] = phR[chan + off];
-      Pd[e] = phP[off];
-      Pm[e] = phP[chan + off];
-      Ss[e] = phS[off];
-      St[e] = phS[chan + off];
+      const int mt = e / g.n_nu, c = e % g.n_nu;
+      const long long rrow = ((long long)(tmom * g.n_om + mt) * nn + k) * nn + cmom * g.n_nu + c;
+      const long long prow = ((long long)(iq * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
+      const long long srow = ((long long)(iqp * g.n_om + mt) * nn + k) * nn + ikp * g.n_nu + c;
+      Rd[mt * RS + c] = phi[rrow];
+      Rm[mt * RS + c] = phi[chan + rrow];
+      Pd[e] = phi[prow];
+      Pm[e] = phi[chan + prow];
+      Ss[e] = phi[2 * chan + srow];
+      St[e] = phi[3 * chan + srow];
     }
     __syncthreads();
-    const long long o2_dm = ((((long long)(iq - pass.qb) * g.n_om) * nn + k) * ld + ikp * g.n_nu) >> 1;
-    const long long o2_st = ((((long long)(iqp - pass.qb) * g.n_om) * nn + k) * ld + ikp * g.n_nu) >> 1;
-    const int xb_dm = iq * g.n_om * g.n + ikp * g.n_nu, xb_st = iqp * g.n_om * g.n + ikp * g.n_nu;
     for (int e = threadIdx.x; e < NB; e += blockDim.x) {
       const int mi = (int)__umulhi((unsigned)e, nnu_magic), npi = e - mi * g.n_nu;
-      const int off2 = mi * half_oslab + (npi >> 1);  // pair offset of (mi, k' pair) in a step
-      const int xoff = mi * g.n + npi;
       const int m = g.m_lo + mi, np_ = g.n_lo + npi;
       const int mt = np_ - n;  // transfer k' - k of maps A and C
       const bool inT = (mt >= g.m_lo && mt <= g.m_hi);
@@ -297,14 +275,16 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
         Bt = to_c<S, C>(St[(mb - g.m_lo) * g.n_nu + npi]);
       }
       const C od = to_c<S, C>(Pd[e]), om = to_c<S, C>(Pm[e]);
-      const C Gd = lam_at<C>(lam, 0, l0, m, n, np_) + (-0.5f) * Ad + (-1.5f) * Am + 0.5f * Bs + 1.5f * Bt;
-      const C Gm = lam_at<C>(lam, 1, l1, m, n, np_) + (-0.5f) * Ad + 0.5f * Am + (-0.5f) * Bs + 0.5f * Bt;
+      const C Gd = lam_at<TAB, C>(lam, 0, l0, m, n, np_) + (-0.5f) * Ad + (-1.5f) * Am + 0.5f * Bs + 1.5f * Bt;
+      const C Gm = lam_at<TAB, C>(lam, 1, l1, m, n, np_) + (-0.5f) * Ad + 0.5f * Am + (-0.5f) * Bs + 0.5f * Bt;
       const C Fd = Gd + od, Fm = Gm + om;
-      const C xq = xph_[xb_dm + xoff];
-      wr.put(o2_dm + off2, cmul(Gd, xq), Fd);
-      wr.put(ochan2 + o2_dm + off2, cmul(Gm, xq), Fm);
+      const int Q = iq * g.n_om + mi;
+      const long long o_dm = ((long long)(Q - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
+      const C xq = (xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
+      out.put(o_dm, cmul(Gd, xq), Fd);
+      out.put(ochan + o_dm, cmul(Gm, xq), Fm);
       // Eq. PA_Sigma, ph part: G(k+q) X_ph(Q,k') [F_d - F_m - (Lambda0_d - Lambda0_m)]
-      const C gkq = gtab[cmom * g.n_g + (n + m - g.g_lo)];
+      const C gkq = (gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
       acc = cfma(cmul(gkq, xq), Fd - Fm - twoU, acc);
       }
       if (do_st) {
@@ -327,14 +307,16 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
         Dm = to_c<S, C>(Pm[(md - g.m_lo) * g.n_nu + npi]);
       }
       const C os = to_c<S, C>(Ss[e]), ot = to_c<S, C>(St[e]);
-      const C Gs = lam_at<C>(lam, 2, l2, m, n, np_) + 0.5f * Cd + (-1.5f) * Cm + 0.5f * Dd + (-1.5f) * Dm;
-      const C Gt = lam_at<C>(lam, 3, l3, m, n, np_) + (-0.5f) * Cd + (-0.5f) * Cm + 0.5f * Dd + 0.5f * Dm;
+      const C Gs = lam_at<TAB, C>(lam, 2, l2, m, n, np_) + 0.5f * Cd + (-1.5f) * Cm + 0.5f * Dd + (-1.5f) * Dm;
+      const C Gt = lam_at<TAB, C>(lam, 3, l3, m, n, np_) + (-0.5f) * Cd + (-0.5f) * Cm + 0.5f * Dd + 0.5f * Dm;
       const C Fs = Gs + os, Ft = Gt + ot;
-      const C xqp = xpp_[xb_st + xoff];
-      wr.put(2 * ochan2 + o2_st + off2, (-0.5f) * cmul(Gs, xqp), Fs);
-      wr.put(3 * ochan2 + o2_st + off2, 0.5f * cmul(Gt, xqp), Ft);
+      const int Qp = iqp * g.n_om + mi;
+      const long long o_st = ((long long)(Qp - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
+      const C xqp = (xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
+      out.put(2 * ochan + o_st, (-0.5f) * cmul(Gs, xqp), Fs);
+      out.put(3 * ochan + o_st, 0.5f * cmul(Gt, xqp), Ft);
       // pp part: G(q'-k) X_pp(Q',k') [F_s + F_t - (Lambda0_s + Lambda0_t)]
-      const C gqk = gtab[pqk * g.n_g + (m - n - 1 - g.g_lo)];
+      const C gqk = (gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
       acc = cfma(cmul(gqk, xqp), Fs + Ft - twoU, acc);
       }
     }
@@ -370,9 +352,9 @@ cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, b
   return cudaGetLastError();
 }
 
-template <typename S, typename C, bool PL>
+template <typename S, typename C, bool PL, bool TAB>
 static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, Lam lam, const Pass &p, long long ps) {
-  auto kfn = assemble_kernel<S, C, PL>;
+  auto kfn = assemble_kernel<S, C, PL, TAB>;
   const size_t sm = assemble_smem_bytes(g, sizeof(S) == sizeof(float2));
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -395,18 +377,26 @@ static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, L
 
 cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p) {
   Lam lam;
+  bool tab = false;
   for (int r = 0; r < 4; ++r) {
     lam.l[r] = make_double2(lam4[2 * r], lam4[2 * r + 1]);
     lam.tab[r] = b.lam_tab[r];
     lam.nl[r] = b.lam_nl[r];
+    tab = tab || b.lam_tab[r];
   }
   // plane stride: fixed by the buffer size (q_chunk momenta), which the tensor maps assume,
   // also for a last pass with fewer momenta
   const long long ps = 4LL * b.q_chunk * g.n_om * g.n * (long long)b.ld;
   switch (b.vfmt) {
-    case V_C128: return assemble_launch<double2, double2, false>(st, g, b, lam, p, ps);
-    case V_C64: return assemble_launch<float2, float2, false>(st, g, b, lam, p, ps);
-    default: return assemble_launch<float2, float2, true>(st, g, b, lam, p, ps);
+    case V_C128:
+      return tab ? assemble_launch<double2, double2, false, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<double2, double2, false, false>(st, g, b, lam, p, ps);
+    case V_C64:
+      return tab ? assemble_launch<float2, float2, false, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<float2, float2, false, false>(st, g, b, lam, p, ps);
+    default:
+      return tab ? assemble_launch<float2, float2, true, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<float2, float2, true, false>(st, g, b, lam, p, ps);
   }
 }
 
