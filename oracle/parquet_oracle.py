@@ -349,7 +349,8 @@ def assemble(g: Grid, phi, K, lam, Qs=None, ks=None):
     for r in range(4):
         lam_r = lam[r][Qs][:, ks] if np.ndim(lam[r]) == 3 else lam[r]  # tabulated or scalar
         gamma[r] = parquet_gamma(g, r, lam_r, lookup, k3, n3, kp3, np3, q3, m3)
-    return gamma, gamma + phi[:, Qs][:, :, ks]
+    # the selected slices and rows only (a broadcast state is never materialised whole)
+    return gamma, gamma + phi[np.ix_(np.arange(4), Qs, ks)]
 
 
 def aux_vertex_minus_lambda0(g: Grid, K, r, k, n, kp, np_, q, m):

@@ -203,14 +203,17 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
     ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 3 * TOL_SPLIT, 15 * TOL_SPLIT),
     # the default scheme (BF16 operands, half as many accumulator updates per k): Sigma and F
     # within the 1e-6 target; Phi, the raw product, at the TF32x3 bound
-    ("square8_u2_b4", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT)])
+    ("square8_u2_b4", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT),
+    # the large solve (n = 1536, 116 GB of Phi): several passes over the q-momenta, so F is
+    # kept for the last pass only and is checked on the sampled slices that fall in it
+    ("square8_u3_b8_nu24", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT)])
 def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
     """The benchmark workloads at full size, in the launch configuration bench.py
     times: iterations 1 and 2 from the zero state, compared on sampled transfer
     slices (Phi, F) and sampled self-energy outputs.  The oracle holds the zero
     state and the first iterate (constant in k, k' per Q by the worked example of
     Sec. II.A) as broadcast views, so it needs no full-size host arrays."""
-    from paper_1510_03330_gb300.binding import Solver
+    from paper_1510_03330_gb300.binding import ParquetError, Solver
 
     p = CONFIGS[name]
     g = O.make_grid(p)
@@ -218,13 +221,22 @@ def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
     Qs = np.array(sorted({0, p.n_Q - 1, int(rng.integers(p.n_Q)), int(rng.integers(p.n_Q))}))
     outs = [(0, g.e_lo), (int(rng.integers(g.nk)), 0), (g.nk - 1, g.n_hi)]
     shape = (4, p.n_Q, p.n, p.n)
+    def kept_F(s):
+        # every sampled slice of a single-pass solve; the last pass's slices of a multi-pass one
+        out = {}
+        for Q in Qs:
+            try:
+                out[Q] = [s.F(r, Q) for r in range(4)]
+            except ParquetError:
+                pass
+        assert p.n_Q - 1 in out
+        return out
+
     with Solver(p, precision=precision) as s:
         s.iterate(1)
-        gpu1 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs},
-                "F": {Q: [s.F(r, Q) for r in range(4)] for Q in Qs}}
+        gpu1 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs}, "F": kept_F(s)}
         s.iterate(1)
-        gpu2 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs},
-                "F": {Q: [s.F(r, Q) for r in range(4)] for Q in Qs}}
+        gpu2 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs}, "F": kept_F(s)}
     a = p.mix
     # iteration 1 from the zero state
     zero = np.broadcast_to(np.zeros((), complex), shape)
@@ -236,7 +248,8 @@ def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
         # four channels (Psi_t, a difference of channels, is far smaller than the others)
         scale = max(np.abs(refs[i][r]).max() for i in range(len(Qs)) for r in range(4))
         for r in range(4):
-            err = max(np.abs(gpu[Q][r] - refs[i][r]).max() for i, Q in enumerate(Qs))
+            err = max(np.abs(gpu[Q][r] - refs[i][r]).max() for i, Q in enumerate(Qs) if Q in gpu)
+            print(what, r, err / scale)
             assert err <= bound * scale + 1e-300, (what, r, err, scale)
 
     check(gpu1["phi"], [[a * phi1[r, i] for r in range(4)] for i in range(len(Qs))], tol_phi, "phi1")
