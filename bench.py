@@ -40,9 +40,10 @@ DEFAULT_PRECISION = SPLIT_BF16X3
 DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulate)",
          SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
 # DRAM bytes of one launch / algorithmic bytes, from ncu captures on the 4x4 lattice
-# (profiles/bse_*_square4_u2_b5.md, profiles/assemble_*_square4_u2_b5.md)
+# (profiles/bse_*_square4_u2_b5.md, profiles/assemble_bf16x3_square4_u2_b5.md)
 BSE_TRAFFIC = {SPLIT_TF32X3: 0.986, SPLIT_BF16X3: 0.978}
-REMAP_TRAFFIC = {FP64: 1.112, SPLIT_TF32X3: 1.052, SPLIT_BF16X3: 1.064}
+# (complex-output assemblies changed after their captures: no figure until taken again)
+REMAP_TRAFFIC = {SPLIT_BF16X3: 1.064}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
 LAUNCHES_PER_ITER = 18

@@ -92,3 +92,7 @@ def test_batch_arguments_are_checked_without_touching_the_gpu(lib):
     assert "tile_cols" in lib.pq_last_error(None).decode()
     assert lib.pq_batch_iterate(None, 1, None) == binding.PQ_EINVAL
     lib.pq_batch_destroy(None)
+
+
+def test_set_lambda_without_context_is_rejected(lib):
+    assert lib.pq_set_Lambda(None, 0, None, 2) == binding.PQ_EINVAL
