@@ -143,7 +143,7 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
   mark(1);
   CK(pq::launch_bubbles(st, g, b));
   mark(2);
-  CK(pq::launch_kernels_extract(st, g, b, c->c64));
+  CK(pq::launch_kernels_extract(st, g, b, c->c64, b.vfmt == pq::V_BF16P && c->krow_ok));
   mark(3);
   CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
   mark(4);
@@ -172,6 +172,8 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
       cudaEventRecord(c->pev[3 * ip + 1], st);
     }
     void *phi_out = fused ? b.phi : b.phi_new;
+    if (b.vfmt == pq::V_BF16P && ip == 0)  // the products of this iteration sum the new Phi's row edges
+      CK(cudaMemsetAsync(b.krow, 0, sizeof(double2) * 4 * (size_t)g.n * g.nQ, st));
     if (!bse) {
       // left to the caller
     } else if (b.vfmt == pq::V_BF16P) {
@@ -210,6 +212,7 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
     c->chi_ready = true;
   }
   mark(8);
+  if (b.vfmt == pq::V_BF16P) c->krow_ok = true;
   return PQ_OK;
 }
 
@@ -414,6 +417,7 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.k1, cs * 4 * g.nQ},
       {(void **)&b.k2row, cs * 4 * (size_t)g.n * g.nQ},
       {(void **)&b.k2col, cs * 4 * (size_t)g.n * g.nQ},
+      {(void **)&b.krow, b.vfmt == pq::V_BF16P ? cs * 4 * (size_t)g.n * g.nQ : 0},
       {(void **)&b.dfpart, cs * (size_t)g.n * g.nk},
       {(void **)&b.scal, 8 * sizeof(double)},
       {(void **)&b.s1_R, cs * g.nk * 2 * (size_t)z.M},
@@ -521,6 +525,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       e.phi_in = (const float2 *)cur;
       e.phi_out = (float2 *)nxt;
       e.alpha = (float)g.mix;
+      e.n_nu = g.n_nu;
+      e.krow = b.krow;
     }
     c->prob_host = tab[0];
     if (s == PQ_OK) {
@@ -713,6 +719,7 @@ pq_status pq_sigma_second_order(pq_ctx *c, const double *sigma_c128, double *out
 pq_status pq_set_state(pq_ctx *c, const double *phi, const double *sigma) {
   if (!c) return PQ_EINVAL;
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (phi) c->krow_ok = false;  // the row sums belong to the replaced Phi
   CK(cudaStreamSynchronize(c->st));
   if (sigma) CK(cudaMemcpy(c->b.sigma, sigma, sizeof(double2) * c->g.nk * c->g.n_ext, cudaMemcpyHostToDevice));
   if (phi) {

@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float alpha = P.alpha, beta = 1.0f - alpha;
       const long long slab = (long long)(T.z / P.zc) * P.phi_cs + P.phi_q0 + T.z % P.zc;
       const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * G::ACC_COLS;
+      // the new Phi of this row at the frequency edges (n' = n_lo, n_hi) of each k' block:
+      // summed here, the next iteration's K2row (Sec. II.A) needs no strided reads of Phi
+      const int nnu = P.n_nu;
+      float rsx = 0.f, rsy = 0.f;
 #pragma unroll 1
       for (int c = CW * half; c < CW * half + CW; c += 16) {
         float cr[16], ci[16];
@@ -249,6 +253,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const float2 *pi = P.phi_in + off;
           float2 *po = P.phi_out + off;
           const int lim = n - (T.col0 + c);
+          int ph = (T.col0 + c) % nnu;  // frequency index of the column within its k' block
+          auto edge = [&](float x, float y) {
+            if (ph == 0 || ph == nnu - 1) {
+              rsx += x;
+              rsy += y;
+            }
+            ph = ph + 1 == nnu ? 0 : ph + 1;
+          };
           if (lim >= 16) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
@@ -258,17 +270,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               o.z = alpha * cr[i + 1] + beta * o.z;
               o.w = alpha * ci[i + 1] + beta * o.w;
               *reinterpret_cast<float4 *>(po + i) = o;
+              edge(o.x, o.y);
+              edge(o.z, o.w);
             }
           } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               if (i < lim) {
                 const float2 o = pi[i];
-                po[i] = make_float2(alpha * cr[i] + beta * o.x, alpha * ci[i] + beta * o.y);
+                const float2 v = make_float2(alpha * cr[i] + beta * o.x, alpha * ci[i] + beta * o.y);
+                po[i] = v;
+                edge(v.x, v.y);
               }
             }
           }
         }
+      }
+      if (P.krow && row < n) {
+        double2 *dst = P.krow + ((long long)(T.z / P.zc) * n + row) * P.phi_cs + P.phi_q0 + T.z % P.zc;
+        atomicAdd(&dst->x, (double)rsx);
+        atomicAdd(&dst->y, (double)rsy);
       }
       tc::fence_before_sync();
       tc::mbar_arrive_cta(&acc_empty[b]);

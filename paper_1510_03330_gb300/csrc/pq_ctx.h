@@ -33,6 +33,7 @@ struct pq_ctx {
   bool chi_ready = false;        // chi computed during the last iteration (several passes)
   pq::BseProblem prob_host{};    // the single-pass entry of the table (for batches)
   bool in_batch = false;         // a batch holds this context: pq_iterate is refused
+  bool krow_ok = false;          // BF16x3: b.krow holds the edge row sums of the current Phi
 };
 
 

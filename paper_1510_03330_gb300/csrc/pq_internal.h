@@ -56,6 +56,7 @@ struct Buffers {
   //   fv planes (Re h, Im h, Re l, Im l, Re r, Im r) with x = h + l + r.
   const void *lam_tab[4] = {};  // tabulated local Lambda per channel (arithmetic type of the assembly)
   int lam_nl[4] = {};
+  double2 *krow = nullptr;       // BF16x3: edge row sums of Phi accumulated by the BSE epilogue
   int vfmt = 0;
   int ld = 0;                    // row stride of gam and fv (elements)
   int q_chunk = 0;               // q-momenta assembled and multiplied per pass
@@ -108,7 +109,8 @@ cudaError_t launch_sigma_update(cudaStream_t st, const Grid &g, Buffers &b);
 cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int nq);
 
 // vertex steps (pq_vertex.cu)
-cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64);
+// K1/K2 from the state; with rowsums, K2row from the edge row sums the last BSE accumulated
+cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64, bool rowsums = false);
 cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p);
 size_t assemble_smem_bytes(const Grid &g, bool c64);
 
@@ -130,6 +132,8 @@ struct BseProblem {
   const float2 *phi_in;
   float2 *phi_out;
   float alpha;
+  int n_nu;           // fermionic frequencies per momentum block (edge test of the row sums)
+  double2 *krow;      // if set: [r][k][Q] += sum of the new Phi row k over the k' frequency edges
 };
 size_t bse_tma_smem_bytes(int bnc);
 long long bse_tiles(int bnc, int n, int batch);

@@ -32,9 +32,12 @@ __device__ inline double2 ld2(const S *p) {
 }
 
 // K1[r][Q], K2row[r][k][Q], K2col[r][k'][Q]; one block per (Q, r), FP64 sums.
-template <typename S>
+// ROWSUM: the row-edge sums of K2row come from krow ([r][k][Q], accumulated by the BSE
+// epilogue that wrote this Phi) instead of strided reads of Phi.
+template <typename S, bool ROWSUM>
 __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__restrict__ k1,
-                               double2 *__restrict__ k2row, double2 *__restrict__ k2col) {
+                               double2 *__restrict__ k2row, double2 *__restrict__ k2col,
+                               const double2 *__restrict__ krow) {
   __shared__ double2 red[256];
   __shared__ double2 sk1;
   const int Q = blockIdx.x, r = blockIdx.y;
@@ -65,11 +68,18 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
   const double inv = 1.0 / (2.0 * nk);
   for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
     double2 rs = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
-    // unrolled so that the loads of several momentum blocks are in flight together
+    if constexpr (ROWSUM) {
+      rs = krow[((long long)r * g.n + k) * g.nQ + Q];
 #pragma unroll 8
-    for (int b = 0; b < nk; ++b) {
-      rs = rs + ld2(V + k * n + b * nn) + ld2(V + k * n + b * nn + nn - 1);
-      cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+      for (int b = 0; b < nk; ++b)
+        cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+    } else {
+      // unrolled so that the loads of several momentum blocks are in flight together
+#pragma unroll 8
+      for (int b = 0; b < nk; ++b) {
+        rs = rs + ld2(V + k * n + b * nn) + ld2(V + k * n + b * nn + nn - 1);
+        cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+      }
     }
     k2row[((long long)r * g.n + k) * g.nQ + Q] = inv * rs - K1;
     k2col[((long long)r * g.n + k) * g.nQ + Q] = inv * cs - K1;
@@ -343,12 +353,14 @@ size_t assemble_smem_bytes(const Grid &g, bool c64) {
   return (2 * (size_t)g.n_om * (g.n_nu + 2) + 4 * (size_t)g.n_om * g.n_nu + 2 * (size_t)g.n_om) * es;
 }
 
-cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64) {
+cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64, bool rowsums) {
   dim3 grid(g.nQ, 4);
-  if (c64)
-    kernels_kernel<float2><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col);
+  if (c64 && rowsums)
+    kernels_kernel<float2, true><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, b.krow);
+  else if (c64)
+    kernels_kernel<float2, false><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr);
   else
-    kernels_kernel<double2><<<grid, 256, 0, st>>>(g, (const double2 *)b.phi, b.k1, b.k2row, b.k2col);
+    kernels_kernel<double2, false><<<grid, 256, 0, st>>>(g, (const double2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr);
   return cudaGetLastError();
 }
 

@@ -120,3 +120,23 @@ def test_bf16x3_rows_not_multiple_of_eight():
         assert rel(all_phi(s, p), st.phi) < 3e-4
         Fg = np.stack([np.stack([s.F(r, Q) for Q in range(p.n_Q)]) for r in range(4)])
         assert rel(Fg, res.F) < 5e-5
+
+
+def test_bf16x3_row_sums_follow_the_state():
+    """The BF16x3 products sum the new Phi's row edges for the next iteration's kernel
+    functions; after pq_set_state those sums are stale and must not be used.  Two
+    iterations, then a new synthetic state and one more iteration, against the oracle."""
+    from paper_1510_03330_gb300.binding import Solver
+
+    p = P22
+    phi, sig = random_state(p, seed=7)
+    with Solver(p, precision=SPLIT_BF16X3) as s:
+        s.iterate(2)
+        s.set_state(phi, sig)
+        s.iterate(1)
+        res = O.iterate(p, O.State(phi, sig))
+        assert rel(s.sigma(), res.state.sigma) < 5e-5
+        assert rel(all_phi(s, p), res.state.phi) < 3e-4
+        s.iterate(1)  # the row sums of the products just run now serve the kernel functions
+        res2 = O.iterate(p, res.state)
+        assert rel(s.sigma(), res2.state.sigma) < 5e-5
