@@ -44,28 +44,11 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
   const long long n = g.n;
   const S *V = phi + ((long long)r * g.nQ + Q) * n * n;
   const int nn = g.n_nu, nk = g.nk;
-  // first level: four corners, all momentum pairs
-  double2 acc = make_double2(0.0, 0.0);
-  const int ncorner = 4 * nk * nk;
-  for (int c = threadIdx.x; c < ncorner; c += blockDim.x) {
-    int e = c & 3, pair = c >> 2;
-    int a = pair / nk, b = pair % nk;
-    int ra = a * nn + ((e & 1) ? nn - 1 : 0), cb = b * nn + ((e & 2) ? nn - 1 : 0);
-    acc = acc + ld2(V + ra * n + cb);
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    sk1 = (1.0 / ncorner) * red[0];
-    k1[(long long)r * g.nQ + Q] = sk1;
-  }
-  __syncthreads();
-  const double2 K1 = sk1;
   const double inv = 1.0 / (2.0 * nk);
+  double2 *K2r = k2row + (long long)r * g.n * g.nQ + Q, *K2c = k2col + (long long)r * g.n * g.nQ + Q;
+  // edge means of the other leg (momentum averaged), kept until K1 is known; the first level
+  // is their mean over the edge columns, i.e. over the four corners and all momentum pairs
+  double2 acc = make_double2(0.0, 0.0);
   for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
     double2 rs = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
     if constexpr (ROWSUM) {
@@ -81,8 +64,26 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
         cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
       }
     }
-    k2row[((long long)r * g.n + k) * g.nQ + Q] = inv * rs - K1;
-    k2col[((long long)r * g.n + k) * g.nQ + Q] = inv * cs - K1;
+    K2r[(long long)k * g.nQ] = inv * rs;
+    K2c[(long long)k * g.nQ] = inv * cs;
+    const int f = k % nn;
+    if (f == 0 || f == nn - 1) acc = acc + cs;  // corners: edge rows x edge columns
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sk1 = (1.0 / (4.0 * nk * nk)) * red[0];
+    k1[(long long)r * g.nQ + Q] = sk1;
+  }
+  __syncthreads();
+  const double2 K1 = sk1;
+  for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
+    K2r[(long long)k * g.nQ] = K2r[(long long)k * g.nQ] - K1;
+    K2c[(long long)k * g.nQ] = K2c[(long long)k * g.nQ] - K1;
   }
 }
 
