@@ -45,8 +45,9 @@ BSE_TRAFFIC = {SPLIT_TF32X3: 0.986, SPLIT_BF16X3: 0.978}
 # (complex-output assemblies changed after their captures: no figure until taken again)
 REMAP_TRAFFIC = {SPLIT_BF16X3: 1.064}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
-# Sigma~2 (4), parquet assembly (1), Sigma update (1), BSE (1)
-LAUNCHES_PER_ITER = 18
+# Sigma~2 (8: tables, their prefix sums, two output passes), parquet assembly (1),
+# Sigma update (1), BSE (1)
+LAUNCHES_PER_ITER = 22
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, nominal
 
 

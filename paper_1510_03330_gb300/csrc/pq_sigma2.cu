@@ -73,12 +73,26 @@ struct Box {
   int accumulate;
 };
 
-__device__ inline double2 wsum(const double2 *row, int j_lo, int nj, int a, int b) {
-  // sum of row[j - j_lo] over j in [a, b]
+// The tables are turned into inclusive prefix sums along j (FP64), so that every
+// frequency-window sum below is the difference of two entries.
+__global__ void s2_prefix_rows(double2 *__restrict__ t, long long rows, int len) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  double2 *row = t + i * len;
   double2 s = make_double2(0.0, 0.0);
+  for (int j = 0; j < len; ++j) {
+    s = s + row[j];
+    row[j] = s;
+  }
+}
+
+__device__ inline double2 wsum(const double2 *cum, int j_lo, int nj, int a, int b) {
+  // sum of the table row over j in [a, b] (clipped to its range) from its prefix sums
   if (a < j_lo) a = j_lo;
   if (b > j_lo + nj - 1) b = j_lo + nj - 1;
-  for (int j = a; j <= b; ++j) s = s + row[j - j_lo];
+  if (a > b) return make_double2(0.0, 0.0);
+  double2 s = cum[b - j_lo];
+  if (a > j_lo) s = s - cum[a - 1 - j_lo];
   return s;
 }
 
@@ -172,6 +186,11 @@ cudaError_t launch_sigma2(cudaStream_t st, const Grid &g, const Sizes &z, Buffer
   int nt = 256;
   s2_bubble_tables<<<(g.nQ * z.nj + nt - 1) / nt, nt, 0, st>>>(g, z.j_lo, z.nj, b.gtab, b.s2_bph, b.s2_bpp);
   s2_weighted_tables<<<(g.nQ * g.n_nu + nt - 1) / nt, nt, 0, st>>>(g, b.gtab, b.k2col, b.s2_cph, b.s2_cpp);
+  // prefix sums of every row: B tables (rows of nj), C tables (rows of Nnu; cph holds two)
+  s2_prefix_rows<<<(2 * g.nQ + nt - 1) / nt, nt, 0, st>>>(b.s2_bph, g.nQ, z.nj);
+  s2_prefix_rows<<<(2 * g.nQ + nt - 1) / nt, nt, 0, st>>>(b.s2_bpp, g.nQ, z.nj);
+  s2_prefix_rows<<<(2 * g.nQ + nt - 1) / nt, nt, 0, st>>>(b.s2_cph, 2LL * g.nQ, g.n_nu);
+  s2_prefix_rows<<<(g.nQ + nt - 1) / nt, nt, 0, st>>>(b.s2_cpp, g.nQ, g.n_nu);
   // enlarged box over the whole extended range
   Box big{g.bf_lo, g.bf_hi, g.bb_lo, g.bb_hi, g.e_lo, g.e_hi, 1.0, 0};
   int warps = g.nk * (g.e_hi - g.e_lo + 1);
