@@ -93,6 +93,11 @@ typedef struct {
    * buffered for the Jacobi update, chi is computed during the iteration, and
    * pq_get_F serves only the transfers of the last pass. */
   int q_chunk;
+  /* Kernel of the parquet assembly on the BF16x3 path: 0 (default) the tiled kernel,
+   * which writes the operand rows in long contiguous runs, wherever Nnu % 4 == 0; 1 the
+   * general kernel.  Both write the same operands; the dF part of Sigma is summed in
+   * another order. */
+  int assembly;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */

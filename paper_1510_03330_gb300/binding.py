@@ -39,6 +39,7 @@ class Options(C.Structure):
         ("tau_matsubara", C.c_int),
         ("time_steps", C.c_int),
         ("q_chunk", C.c_int),
+        ("assembly", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -158,7 +159,7 @@ class Solver:
     """One parquet solve on the GPU (C ABI: pq_init ... pq_destroy)."""
 
     def __init__(self, p: Params, precision: str = FP64, time_steps: bool = False, use_torch: bool = True,
-                 q_chunk: int = 0):
+                 q_chunk: int = 0, assembly: int = 0):
         lib = load_library()
         self.p = p
         self.lib = lib
@@ -172,6 +173,7 @@ class Solver:
         o.tau_matsubara = p.tau_matsubara
         o.time_steps = 1 if time_steps else 0
         o.q_chunk = q_chunk
+        o.assembly = assembly
         self._alloc = None
         if use_torch:
             import torch

@@ -364,6 +364,11 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     delete c;
     return fail(nullptr, PQ_EINVAL, "q_chunk must be >= 0");
   }
+  if (o.assembly < 0 || o.assembly > 1) {
+    delete c;
+    return fail(nullptr, PQ_EINVAL, "assembly must be 0 (tiled) or 1 (general)");
+  }
+  b.assembly = o.assembly;
 
   if (pq::assemble_smem_bytes(g, c->c64) > 200 * 1024) {
     delete c;

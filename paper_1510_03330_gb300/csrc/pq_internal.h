@@ -58,6 +58,7 @@ struct Buffers {
   int lam_nl[4] = {};
   double2 *krow = nullptr;       // BF16x3: edge row sums of Phi accumulated by the BSE epilogue
   int vfmt = 0;
+  int assembly = 0;              // BF16x3 assembly kernel: 0 tiled where the shape allows, 1 general
   int ld = 0;                    // row stride of gam and fv (elements)
   int q_chunk = 0;               // q-momenta assembled and multiplied per pass
   void *phi_new = nullptr;       // Jacobi target when the transfers run in several passes
@@ -112,6 +113,12 @@ cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int n
 // K1/K2 from the state; with rowsums, K2row from the edge row sums the last BSE accumulated
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64, bool rowsums = false);
 cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p);
+struct Lam;
+// tiled BF16 assembly (pq_assemble_tiled.cu): false / cudaErrorInvalidValue where the shape
+// is not served (Nnu % 4 != 0)
+bool assemble_tiled_ok(const Grid &g);
+cudaError_t launch_assemble_tiled(cudaStream_t st, const Grid &g, Buffers &b, const Lam &lam, const Pass &p,
+                                  long long ps, bool tab);
 size_t assemble_smem_bytes(const Grid &g, bool c64);
 
 // TF32x3 BSE on the tensor cores from complex64 operands (pq_gemm_tc.cu)

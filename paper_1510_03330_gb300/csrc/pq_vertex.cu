@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "pq_common.cuh"
+#include "pq_assemble.cuh"
 #include "pq_internal.h"
 
 namespace pq {
@@ -87,27 +88,6 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
   }
 }
 
-// Fully irreducible vertex: the parquet-approximation constants (U, -U, 2U, 0), and per
-// channel an optional local table on |m| <= nl[r], n, n' in [-nl[r], nl[r] - 1] (Sec. III.A:
-// Lambda from an impurity calculation, supplemented by the constants outside its box),
-// laid out [m + nl][n + nl][n' + nl] in the arithmetic type of the assembly.
-struct Lam {
-  double2 l[4];
-  const void *tab[4];
-  int nl[4];
-};
-
-// Lambda_r at (m, n, n'); without tables (TAB false) the constant, at no cost.
-template <bool TAB, typename C>
-__device__ inline C lam_at(const Lam &lam, int r, C l_r, int m, int n, int np_) {
-  if constexpr (TAB) {
-    const int nl = lam.nl[r];
-    if (lam.tab[r] && m >= -nl && m <= nl && n >= -nl && n < nl && np_ >= -nl && np_ < nl)
-      return ((const C *)lam.tab[r])[((m + nl) * 2 * nl + (n + nl)) * 2 * nl + (np_ + nl)];
-  }
-  return l_r;
-}
-
 template <typename C> __device__ inline C cz();
 template <> __device__ inline double2 cz<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ inline float2 cz<float2>() { return make_float2(0.f, 0.f); }
@@ -118,14 +98,6 @@ template <typename C> __device__ inline double2 cdbl(C v);
 template <> __device__ inline double2 cdbl<double2>(double2 v) { return v; }
 template <> __device__ inline double2 cdbl<float2>(float2 v) { return make_double2(v.x, v.y); }
 
-// BF16 rounding (to nearest, ties to even) of finite FP32 values in integer arithmetic:
-// the upper half of u + 0x7FFF + (bit 16 of u).  Identical to the hardware conversion,
-// but it runs on the integer ALU instead of the conversion unit, which is narrow on this
-// part and otherwise bounds the assembly.
-__device__ inline uint32_t bf16_round(float x) {
-  const uint32_t u = __float_as_uint(x);
-  return u + 0x7FFFu + ((u >> 16) & 1u);
-}
 // (k', k'+1) values -> packed BF16 pair (k' in the low half) and the FP32 remainders
 __device__ inline uint32_t split_pair(float x0, float x1, float &r0, float &r1) {
   const uint32_t a = bf16_round(x0), b = bf16_round(x1);
@@ -408,6 +380,7 @@ cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const do
       return tab ? assemble_launch<float2, float2, false, true>(st, g, b, lam, p, ps)
                  : assemble_launch<float2, float2, false, false>(st, g, b, lam, p, ps);
     default:
+      if (b.assembly == 0 && assemble_tiled_ok(g)) return launch_assemble_tiled(st, g, b, lam, p, ps, tab);
       return tab ? assemble_launch<float2, float2, true, true>(st, g, b, lam, p, ps)
                  : assemble_launch<float2, float2, true, false>(st, g, b, lam, p, ps);
   }
