@@ -27,12 +27,31 @@ namespace pq {
 
 namespace {
 
+// Running sum of edge values: FP64 for the FP64 path; for the complex64 path a compensated
+// FP32 sum (Knuth's TwoSum: s + c holds the running sum to about twice FP32 precision), so
+// that no element is converted or added on the FP64 pipe, which is narrow on this part.
 template <typename S>
-__device__ inline double2 ld2(const S *p) {
-  return to_c<S, double2>(*p);
-}
+struct EdgeSum {
+  double2 v = make_double2(0.0, 0.0);
+  __device__ inline void add(S x) { v = v + to_c<S, double2>(x); }
+  __device__ inline double2 get() const { return v; }
+};
+template <>
+struct EdgeSum<float2> {
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+  __device__ static inline void two_sum(float &s, float &c, float x) {
+    const float t = s + x, z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ inline void add(float2 x) {
+    two_sum(sx, cx, x.x);
+    two_sum(sy, cy, x.y);
+  }
+  __device__ inline double2 get() const { return make_double2((double)sx + (double)cx, (double)sy + (double)cy); }
+};
 
-// K1[r][Q], K2row[r][k][Q], K2col[r][k'][Q]; one block per (Q, r), FP64 sums.
+// K1[r][Q], K2row[r][k][Q], K2col[r][k'][Q]; one block per (Q, r).
 // ROWSUM: the row-edge sums of K2row come from krow ([r][k][Q], accumulated by the BSE
 // epilogue that wrote this Phi) instead of strided reads of Phi.
 template <typename S, bool ROWSUM>
@@ -51,20 +70,27 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
   // is their mean over the edge columns, i.e. over the four corners and all momentum pairs
   double2 acc = make_double2(0.0, 0.0);
   for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
-    double2 rs = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
+    double2 rs, cs;
+    EdgeSum<S> es_r, es_c;
     if constexpr (ROWSUM) {
       rs = krow[((long long)r * g.n + k) * g.nQ + Q];
 #pragma unroll 8
-      for (int b = 0; b < nk; ++b)
-        cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+      for (int b = 0; b < nk; ++b) {
+        es_c.add(V[(long long)(b * nn) * n + k]);
+        es_c.add(V[(long long)(b * nn + nn - 1) * n + k]);
+      }
     } else {
       // unrolled so that the loads of several momentum blocks are in flight together
 #pragma unroll 8
       for (int b = 0; b < nk; ++b) {
-        rs = rs + ld2(V + k * n + b * nn) + ld2(V + k * n + b * nn + nn - 1);
-        cs = cs + ld2(V + (long long)(b * nn) * n + k) + ld2(V + (long long)(b * nn + nn - 1) * n + k);
+        es_r.add(V[k * n + b * nn]);
+        es_r.add(V[k * n + b * nn + nn - 1]);
+        es_c.add(V[(long long)(b * nn) * n + k]);
+        es_c.add(V[(long long)(b * nn + nn - 1) * n + k]);
       }
+      rs = es_r.get();
     }
+    cs = es_c.get();
     K2r[(long long)k * g.nQ] = inv * rs;
     K2c[(long long)k * g.nQ] = inv * cs;
     const int f = k % nn;
