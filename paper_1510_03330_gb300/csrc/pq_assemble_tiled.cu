@@ -53,7 +53,28 @@ struct TGeo {
   int oR, oP, oS, oFK, oRing, oBar, smem;  // shared-memory layout (bytes)
   int tx;     // bytes gathered per step
   int ring_n; // threads per block index a (hb * rows)
+  unsigned long long m_per, m_gn, m_nom;  // x / d = (x * m_d) >> 32 for x < 2^16 (d = 3 tiles' copies, G NOmega, NOmega)
 };
+
+__device__ __forceinline__ int mdiv(int x, unsigned long long m) { return (int)(((unsigned long long)x * m) >> 32); }
+
+// Momentum bookkeeping of one step, T_N ints per block b: the transfer groups (and the R
+// column block) its gathers read, and the output rows of the step.  Kept in shared memory so
+// that the lattice additions (integer divisions by L) are done once per block and step.
+enum { T_QR, T_CR, T_QP, T_QS, T_PQK, T_CM, T_Q0, T_N };
+// dm: the gathers of q = qt (the d/m step, or a fused step); else those feeding q' = qt.
+__device__ inline void step_table(const Grid &g, bool dm, int qt, int ik, int p0, int b, int *e) {
+  const int pb = p0 + b;
+  const int qb_ = dm ? qt : ksub(g, ksub(g, qt, ik), pb);  // q of this block's slices
+  const int x = dm ? kadd(g, kadd(g, ik, pb), qt) : qt;    // q' = k + p_b + q: S group, s/t output row
+  e[T_QR] = ksub(g, pb, ik);
+  e[T_CR] = kadd(g, ik, qb_);
+  e[T_QP] = qb_;
+  e[T_QS] = x;
+  e[T_PQK] = ksub(g, x, ik);
+  e[T_CM] = kadd(g, ik, qt);
+  e[T_Q0] = kadd(g, kadd(g, ik, p0), qt);
+}
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -61,14 +82,14 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                : "memory");
 }
 
-// One gather step, issued by all threads of the CTA (thread 0 posts the byte count).  Per
-// block b the sources are, for the d/m step of q = qt (dm):
+// One gather step, issued by all threads of the CTA (thread 0 posts the byte count), with
+// the sources of the step table tb.  Per block b, for the d/m step of q = qt:
 //   R from transfer group p_b - k at column block k + qt, P from group qt, S from k + p_b + qt;
 // for the s/t step of q' = qt, with q_b = qt - k - p_b:
 //   R from group p_b - k at column block k + q_b, P from group q_b, S from group qt.
 // P and S take column block p_b.
-__device__ inline void issue_gather(const Grid &g, const TGeo &t, bool dm, int qt, const float2 *phi, int k, int ik,
-                                    int p0, float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar) {
+__device__ inline void issue_gather(const Grid &g, const TGeo &t, const int *tb, const float2 *phi, int k, int p0,
+                                    float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar) {
   const int G = t.G, nom = g.n_om, nnu = g.n_nu;
   const long long nn = g.n, chan = (long long)g.nQ * nn * nn;
   const uint32_t b = tc::smem_u32(bar);
@@ -78,18 +99,18 @@ __device__ inline void issue_gather(const Grid &g, const TGeo &t, bool dm, int q
   const int per = 2 * G * nom;
   const uint32_t bytes = (uint32_t)nnu * 8u;
   for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
-    const int tile = i / per, ii = i % per;
-    const int x = ii / (G * nom), a = (ii / nom) % G, mt = ii % nom;
-    const int pb = p0 + a;
-    const int qb_ = dm ? qt : ksub(g, ksub(g, qt, ik), pb);  // q of this block's slices
+    const int tile = mdiv(i, t.m_per), ii = i - tile * per;
+    const int x = mdiv(ii, t.m_gn), rem = ii - x * G * nom;
+    const int a = mdiv(rem, t.m_nom), mt = rem - a * nom;
+    const int *e = tb + a * T_N;
     const float2 *src;
     float2 *dst;
     if (tile == 0) {
-      src = phi + x * chan + ((long long)(ksub(g, pb, ik) * nom + mt) * nn + k) * nn + (long long)kadd(g, ik, qb_) * nnu;
+      src = phi + x * chan + ((long long)(e[T_QR] * nom + mt) * nn + k) * nn + (long long)e[T_CR] * nnu;
       dst = Rt + (x * G + a) * t.RA + mt * t.RS;
     } else {
-      const int qg = tile == 1 ? qb_ : (dm ? kadd(g, kadd(g, ik, pb), qt) : qt);
-      src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)pb * nnu;
+      const int qg = tile == 1 ? e[T_QP] : e[T_QS];
+      src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)(p0 + a) * nnu;
       dst = (tile == 1 ? Pt : St) + (x * nom + mt) * t.PW + a * t.BW;
     }
     bulk_load(tc::smem_u32(dst), src, bytes, b);
@@ -246,6 +267,7 @@ __global__ void __launch_bounds__(TT, 2)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double2 red[TT];
   __shared__ int abort_flag;
+  __shared__ int stab[2][4 * T_N];  // step tables of this step and the next
   float2 *Rt = (float2 *)(smem + t.oR), *Pt = (float2 *)(smem + t.oP), *St = (float2 *)(smem + t.oS);
   float2 *FK = (float2 *)(smem + t.oFK);
   float4 *ring = (float4 *)(smem + t.oRing);
@@ -260,7 +282,6 @@ __global__ void __launch_bounds__(TT, 2)
   const int cu = tid % t.upr, row0 = tid / t.upr;
   const bool worker = tid < t.upr * t.rows;  // the padding threads only take part in the barriers
   const int a = cu / t.hb;
-  const int pa = p0 + a;
   const int col0 = p0 * nnu + 4 * cu;  // first output column of this thread: p_a Nnu + npi0
 
   for (int i = tid; i < 2 * G * nom; i += blockDim.x) {
@@ -268,6 +289,11 @@ __global__ void __launch_bounds__(TT, 2)
     const int Qt = ksub(g, p0 + b, ik) * nom + mt;
     FK[i] = f2(k1[(long long)x * g.nQ + Qt] + k2row[((long long)x * g.n + k) * g.nQ + Qt]);
   }
+  const int nsteps = FUSED ? g.nk : 2 * pass.nq;
+  // step -> (kind, q): FUSED walks q = 0..nk-1 (both kinds); otherwise target qt, d/m then s/t
+  auto step_q = [&](int st) { return FUSED ? st : pass.qb + st / 2; };
+  auto step_dm = [&](int st) { return FUSED || (st & 1) == 0; };
+  if (tid < G) step_table(g, step_dm(0), step_q(0), ik, p0, tid, stab[0] + tid * T_N);
   if (tid == 0) {
     abort_flag = 0;
     tc::mbar_init(bar, 1);
@@ -283,12 +309,12 @@ __global__ void __launch_bounds__(TT, 2)
   float4 *dl = ring + (size_t)8 * t.ring_n * (a * (a - 1) / 2) + row0 * t.hb + cu % t.hb;
   uint32_t phase = 0;
 
-  const int nsteps = FUSED ? g.nk : 2 * pass.nq;
-  for (int step = 0; step < nsteps; ++step) {
-    // step -> (kind, q): FUSED walks q = 0..nk-1 (both kinds); otherwise target qt, d/m then s/t
-    const bool do_dm = FUSED || (step & 1) == 0, do_st = FUSED || (step & 1) == 1;
-    const int qt = FUSED ? step : pass.qb + step / 2;
-    issue_gather(g, t, do_dm, qt, phi, k, ik, p0, Rt, Pt, St, bar);
+  int qy = 0;  // FUSED: y coordinate of q (q = step)
+  for (int step = 0; step < nsteps; ++step, qy = (qy + 1 == g.L) ? 0 : qy + 1) {
+    const bool do_dm = step_dm(step), do_st = FUSED || !do_dm;
+    const int qt = step_q(step);
+    const int *tb = stab[step & 1];
+    issue_gather(g, t, tb, phi, k, p0, Rt, Pt, St, bar);
     if (!tc::mbar_wait_ns(bar, phase, GATHER_WAIT_NS)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
@@ -300,6 +326,8 @@ __global__ void __launch_bounds__(TT, 2)
       return;
     }
     phase ^= 1u;
+    if (tid < G && step + 1 < nsteps)
+      step_table(g, step_dm(step + 1), step_q(step + 1), ik, p0, tid, stab[(step + 1) & 1] + tid * T_N);
 
     for (int mi = row0; worker && mi < nom; mi += t.rows) {
       c.mi = mi;
@@ -309,24 +337,23 @@ __global__ void __launch_bounds__(TT, 2)
         const int Q = qt * nom + mi;
         float2 xq[4];
         load4(xph + (long long)Q * nn + col0, xq);
-        const float2 gkq = gtab[(long long)kadd(g, ik, qt) * g.n_g + (n + m - g.g_lo)];
+        const float2 gkq = gtab[(long long)tb[T_CM] * g.n_g + (n + m - g.g_lo)];
         elems_dm<TAB>(g, c, lam, l0, l1, twoU, xq, gkq, gx, f, acc);
         const long long o = ((long long)(Q - pass.qb * nom) * nn + k) * ld + col0;
         put4(gam, fv, ps, o, gx[0], f[0]);
         put4(gam, fv, ps, ochan + o, gx[1], f[1]);
       }
       if (do_st) {
-        const int qp = FUSED ? kadd(g, kadd(g, ik, pa), qt) : qt;  // q' of this thread's block
+        const int qp = tb[a * T_N + T_QS];  // q' of this thread's block
         const int Qp = qp * nom + mi;
         float2 xqp[4];
         load4(xpp + (long long)Qp * nn + col0, xqp);
-        const float2 gqk = gtab[(long long)ksub(g, qp, ik) * g.n_g + (m - n - 1 - g.g_lo)];
+        const float2 gqk = gtab[(long long)tb[a * T_N + T_PQK] * g.n_g + (m - n - 1 - g.g_lo)];
         elems_st<TAB>(g, c, lam, l2, l3, twoU, xqp, gqk, gx, f, acc);
         if constexpr (FUSED) {
           // Block 0 of row q0 = k + p_0 + q is produced now; block a >= 1 of that row was
           // produced a steps ago (same lattice row of q) and waits in the delay line.  All
           // blocks of the row are stored by one put4 (one warp instruction per plane).
-          const int qy = qt % g.L;
           float4 *sl = dl + (size_t)8 * t.ring_n * (a > 0 ? qy % a : 0);
           if (a == 0 || qy >= a) {
             float2 wg[2][4], wf[2][4];
@@ -346,7 +373,7 @@ __global__ void __launch_bounds__(TT, 2)
                 wf[h][2] = make_float2(v1.x, v1.y), wf[h][3] = make_float2(v1.z, v1.w);
               }
             }
-            const int q0 = kadd(g, kadd(g, ik, p0), qt);
+            const int q0 = tb[T_Q0];
             const long long o = ((long long)(q0 * nom + mi) * nn + k) * ld + col0;
             put4(gam, fv, ps, 2 * ochan + o, wg[0], wf[0]);
             put4(gam, fv, ps, 3 * ochan + o, wg[1], wf[1]);
@@ -426,6 +453,10 @@ bool tiled_geo(const Grid &g, bool fused, TGeo &t) {
   t.oBar = o;
   t.smem = o + 8;
   t.tx = 6 * G * g.n_om * g.n_nu * 8;
+  auto magic = [](unsigned d) { return (unsigned long long)(0xFFFFFFFFull / d) + 1ull; };
+  t.m_per = magic(2 * G * g.n_om);
+  t.m_gn = magic(G * g.n_om);
+  t.m_nom = magic(g.n_om);
   return t.smem <= 200 * 1024;
 }
 
