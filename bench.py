@@ -39,11 +39,12 @@ DEFAULT_WORKLOAD = "square8_u2_b4"
 DEFAULT_PRECISION = SPLIT_BF16X3
 DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulate)",
          SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
-# DRAM bytes of one launch / algorithmic bytes, from ncu captures on the 4x4 lattice
-# (profiles/bse_*_square4_u2_b5.md, profiles/assemble_bf16x3_square4_u2_b5.md)
-BSE_TRAFFIC = {SPLIT_TF32X3: 0.986, SPLIT_BF16X3: 0.978}
-# (complex-output assemblies changed after their captures: no figure until taken again)
-REMAP_TRAFFIC = {SPLIT_BF16X3: 1.064}
+# DRAM bytes of one launch / algorithmic bytes.  Measured at full size (one-pass ncu capture
+# of the launch itself, profiles/dram_square8_u2_b4_bf16x3.md) for the workload and scheme
+# it was taken on; otherwise from a capture on the 4x4 lattice scaled by the launch's size
+# (profiles/bse_split_tf32x3_square4_u2_b5.md); kernels changed since a capture have none.
+FULL_TRAFFIC = {("square8_u2_b4", SPLIT_BF16X3): {"bse": 1.212, "assemble": 1.216}}
+BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (8: tables, their prefix sums, two output passes), parquet assembly (1),
 # Sigma update (1), BSE (1)
@@ -472,6 +473,7 @@ def main():
     steps = {k: v / a.steps for k, v in step_sum.items() if k != "total"}
     top = max(steps, key=steps.get)
     bse_flops = 8.0 * n**3 * 4 * nQ
+    full_tr = FULL_TRAFFIC.get((a.workload, a.precision), {}) if a.q_chunk == 0 else {}
     # remap: read 4 Phi, write the BSE operands of 4 channels; BF16 planes are 8 bytes per
     # complex for Gamma X and 12 for F (three pieces), otherwise one complex of esz each
     remap_bytes = 4.0 * nQ * n * n * (esz + (20 if a.precision == SPLIT_BF16X3 else 2 * esz))
@@ -484,18 +486,20 @@ def main():
     else:
         ratio = {SPLIT_TF32X3: 1.1 / 2.25, SPLIT_BF16X3: 1.0, SPLIT_BF16X6: 1.0}[a.precision]
         peak = pk["bf16_tflops"] * ratio
-        # DRAM bytes per launch: ncu captures of each kernel on the 4x4 lattice, as a multiple of
-        # the algorithmic 32 n^2 bytes per GEMM (read A, B, Phi; write Phi), scaled by n^2 x batch
-        tr = BSE_TRAFFIC.get(a.precision)
+        # DRAM bytes per launch as a multiple of the algorithmic 32 n^2 bytes per GEMM (read A,
+        # B, Phi; write Phi)
+        tr, tsrc = full_tr.get("bse"), "ncu capture of this launch at full size"
+        if tr is None and a.precision in BSE_TRAFFIC:
+            tr, tsrc = BSE_TRAFFIC[a.precision], "ncu capture on the 4x4 lattice scaled by n^2 x batch"
         bse_roof = {"bound": "tensor", "achieved": bse_tflops, "peak": peak, "unit": "TFLOP/s",
                     "frac": bse_tflops / peak, "traffic": tr * 32.0 * n * n * 4 * nQ if tr else None,
-                    "traffic_source": "ncu capture on the 4x4 lattice scaled by n^2 x batch",
+                    "traffic_source": tsrc if tr else None,
                     "executed_tensor_frac": 3.0 * bse_tflops / peak,
                     "peak_source": f"{src} bf16 burst x nominal ratio {ratio:.3f}"}
-    tr = REMAP_TRAFFIC.get(a.precision)
+    tr = full_tr.get("assemble")
     remap_roof = {"bound": "hbm", "achieved": remap_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                   "frac": remap_gbs / pk["hbm_gbs"], "traffic": tr * remap_bytes if tr else None,
-                  "traffic_source": "ncu capture on the 4x4 lattice, as a multiple of the algorithmic bytes, scaled",
+                  "traffic_source": "ncu capture of this launch at full size" if tr else None,
                   "peak_source": f"{src} copy bandwidth"}
     roof = bse_roof if top == "bse" else (remap_roof if top == "assemble" else bse_roof)
     roof = dict(roof, kernel=top)
