@@ -422,16 +422,19 @@ __global__ void __launch_bounds__(TT, 2)
 
 int align128(int x) { return (x + 127) & ~127; }
 
-// Tile geometry; false if the shape is not served by the tiled kernel (Nnu % 4 != 0, or a
-// row of thread columns wider than a CTA).  fused: the delay line is wanted.
-bool tiled_geo(const Grid &g, bool fused, TGeo &t) {
-  if (g.n_nu % 4 != 0) return false;
-  const int G = (g.L % 4 == 0) ? 4 : (g.L % 2 == 0) ? 2 : 1;
+// Dynamic shared memory of a CTA such that two fit on an SM (228 KB, less 1 KB reserved
+// and the static arrays per CTA).
+constexpr int SMEM_TWO_PER_SM = (228 * 1024) / 2 - 1024 - 4352;
+
+// Tile geometry for G blocks; false if it does not serve the shape.
+bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   t.G = G;
   t.hb = g.n_nu / 4;
   t.upr = G * t.hb;
   if (t.upr > TT) return false;
-  t.rows = std::min(g.n_om, TT / t.upr);
+  // rows of a sweep balanced over the sweeps that NOmega needs
+  const int sweeps = (g.n_om + TT / t.upr - 1) / (TT / t.upr);
+  t.rows = (g.n_om + sweeps - 1) / sweeps;
   t.nthr = (t.upr * t.rows + 31) / 32 * 32;
   if (fused && t.rows < g.n_om) return false;
   t.RS = g.n_nu + 2;
@@ -458,6 +461,27 @@ bool tiled_geo(const Grid &g, bool fused, TGeo &t) {
   t.m_gn = magic(G * g.n_om);
   t.m_nom = magic(g.n_om);
   return t.smem <= 200 * 1024;
+}
+
+// Geometry of the launch; false if the shape is not served by the tiled kernel (Nnu % 4 != 0).
+// G is the widest block count dividing L (4, 2, 1) whose CTA leaves room for a second one on
+// the SM, else the widest that fits at all.  fused: the delay line is wanted.
+bool tiled_geo(const Grid &g, bool fused, TGeo &t) {
+  if (g.n_nu % 4 != 0) return false;
+  bool any = false;
+  TGeo first;
+  for (int G = 4; G >= 1; G /= 2) {
+    if (g.L % G != 0) continue;
+    TGeo c;
+    if (!tiled_geo_g(g, fused, G, c)) continue;
+    if (c.smem <= SMEM_TWO_PER_SM) {
+      t = c;
+      return true;
+    }
+    if (!any) first = c, any = true;
+  }
+  if (any) t = first;
+  return any;
 }
 
 template <bool FUSED, bool TAB>
