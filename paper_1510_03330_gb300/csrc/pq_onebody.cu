@@ -178,14 +178,46 @@ __device__ inline double2 f_elem(const void *fv, long long ps, long long e) {
   }
 }
 
+// Element e of the F operand buffer of a split path in FP32: the complex64 value, or the sum
+// of the three BF16 pieces (h + l is exact; adding r rounds once, at 2^-24 relative).
+template <int FMT>
+__device__ inline float2 f_elem32(const void *fv, long long ps, long long e) {
+  if constexpr (FMT == V_C64) {
+    return ((const float2 *)fv)[e];
+  } else {
+    const uint16_t *p = (const uint16_t *)fv;
+    auto bf = [&](long long i) { return __uint_as_float((uint32_t)p[i] << 16); };
+    return make_float2((bf(e) + bf(2 * ps + e)) + bf(4 * ps + e), (bf(ps + e) + bf(3 * ps + e)) + bf(5 * ps + e));
+  }
+}
+
+// Running FP32 sum with its rounding error kept (Knuth's TwoSum): s + c is the exact sum of
+// the terms added, to about twice FP32 precision.
+struct Sum2 {
+  float s = 0.f, c = 0.f;
+  __device__ inline void add(float x) {
+    const float t = s + x, z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ inline void add(const Sum2 &o) {
+    add(o.s);
+    c += o.c;
+  }
+};
+
 // chi_r(Q) = -sum_k X(k) - sum_{k,k'} X(k) F_r(Q)[k][k'] X(k') for the slices in the operand
 // buffer (nq q-momenta from qb), in two deterministic stages: partial sums over blocks of
 // CHI_ROWS rows (one warp per row at a time, lanes along k'), then their sum per (r, Q).
+// FP64 path: FP64 throughout.  Split paths: the row sums sum_k' F X in FP32 products with
+// compensated FP32 accumulation (no per-element work on the FP64 pipe, which is narrow on
+// this part), each row's result then combined in FP64.
 constexpr int CHI_ROWS = 64;
 
 template <int FMT>
 __global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, int qb, int nq, int q_chunk,
                                    const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
+                                   const float2 *__restrict__ xph32, const float2 *__restrict__ xpp32,
                                    double2 *__restrict__ part) {
   __shared__ double2 red[8];
   const int chunk = blockIdx.x, Ql = blockIdx.y, r = blockIdx.z, Q = qb * g.n_om + Ql;
@@ -197,10 +229,29 @@ __global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, 
   const int k_end = min(g.n, (chunk + 1) * CHI_ROWS);
   double2 acc = make_double2(0.0, 0.0);
   for (int k = chunk * CHI_ROWS + warp; k < k_end; k += 8) {
-    double2 rs = make_double2(0.0, 0.0);
-    for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem<FMT>(fv, ps, base + (long long)k * ld + kp), X[kp], rs);
-    for (int o = 16; o > 0; o >>= 1)
-      rs = make_double2(rs.x + __shfl_xor_sync(0xffffffffu, rs.x, o), rs.y + __shfl_xor_sync(0xffffffffu, rs.y, o));
+    double2 rs;
+    if constexpr (FMT == V_C128) {
+      rs = make_double2(0.0, 0.0);
+      for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem<FMT>(fv, ps, base + (long long)k * ld + kp), X[kp], rs);
+      for (int o = 16; o > 0; o >>= 1)
+        rs = make_double2(rs.x + __shfl_xor_sync(0xffffffffu, rs.x, o), rs.y + __shfl_xor_sync(0xffffffffu, rs.y, o));
+    } else {
+      const float2 *X32 = (r < 2 ? xph32 : xpp32) + (long long)Q * g.n;
+      Sum2 re, im;
+      for (int kp = lane; kp < g.n; kp += 32) {
+        const float2 f = f_elem32<FMT>(fv, ps, base + (long long)k * ld + kp), x = X32[kp];
+        re.add(fmaf(f.x, x.x, -f.y * x.y));
+        im.add(fmaf(f.x, x.y, f.y * x.x));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        Sum2 ore, oim;
+        ore.s = __shfl_xor_sync(0xffffffffu, re.s, o), ore.c = __shfl_xor_sync(0xffffffffu, re.c, o);
+        oim.s = __shfl_xor_sync(0xffffffffu, im.s, o), oim.c = __shfl_xor_sync(0xffffffffu, im.c, o);
+        re.add(ore);
+        im.add(oim);
+      }
+      rs = make_double2((double)re.s + (double)re.c, (double)im.s + (double)im.c);
+    }
     if (lane == 0) acc = acc + cfma(X[k], rs, X[k]);
   }
   if (lane == 0) red[warp] = acc;
@@ -298,11 +349,14 @@ cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int n
   if (4 * slabs * nchunk > b.chi_part_elems) return cudaErrorInvalidValue;
   dim3 grid(nchunk, (unsigned)slabs, 4);
   if (b.vfmt == V_C128)
-    chi_partial_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
+    chi_partial_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, nullptr, nullptr,
+                                                     b.chi_part);
   else if (b.vfmt == V_C64)
-    chi_partial_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
+    chi_partial_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.xph32, b.xpp32,
+                                                    b.chi_part);
   else
-    chi_partial_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.chi_part);
+    chi_partial_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.xph32,
+                                                      b.xpp32, b.chi_part);
   chi_sum_kernel<<<nblk(4 * slabs, 256), 256, 0, st>>>(g, qb, nq, nchunk, b.chi_part, b.chi);
   return cudaGetLastError();
 }
