@@ -98,6 +98,13 @@ typedef struct {
    * general kernel.  Both write the same operands; the dF part of Sigma is summed in
    * another order. */
   int assembly;
+  /* Kernel approximation of the fill and of F~ (Sec. II.A): 0 or 2 (default) second
+   * level, K1 + K2; 1 first level, K1 only. */
+  int kernel_level;
+  /* Frequency edge the second-level kernels are read at: 0 (default) the mean of the
+   * lower and upper edges of the box; 1 the lower edge alone (the paper's example of
+   * one edge), with K1 at the lower corner. */
+  int edge_rule;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */

@@ -255,16 +255,26 @@ def extract_kernels(g: Grid, phi):
     K2row[r, Q, k], K2col[r, Q, k']: second-level kernels minus K1, Phi_r at the
     two frequency edges of the other leg; the level-2 approximation is
     K1 + K2row(k) + K2col(k').
+
+    Ablations of the same section (Params.edge_rule, Params.kernel_level): with
+    edge_rule "lower" the second-level kernels are Phi_r at the lower frequency edge
+    of the other leg alone, as in the paper's example of one edge, and K1 the corner
+    at the lower edges of both legs; with kernel_level 1 only the background is kept
+    (first-level approximation, K2 = 0).
     """
     p = g.p
     nk, nn = g.nk, p.n_nu
     v = phi.reshape(4, p.n_Q, nk, nn, nk, nn)
-    edges = [0, nn - 1]
-    K1 = sum(v[:, :, :, a, :, b].mean(axis=(2, 3)) for a in edges for b in edges) / 4.0
-    rows = sum(v[:, :, :, :, :, b].mean(axis=4) for b in edges) / 2.0  # (4, Q, k, n)
-    cols = sum(v[:, :, :, a, :, :].mean(axis=2) for a in edges) / 2.0  # (4, Q, k', n')
+    edges = [0] if getattr(p, "edge_rule", "both") == "lower" else [0, nn - 1]
+    ne = len(edges)
+    K1 = sum(v[:, :, :, a, :, b].mean(axis=(2, 3)) for a in edges for b in edges) / (ne * ne)
+    rows = sum(v[:, :, :, :, :, b].mean(axis=4) for b in edges) / ne  # (4, Q, k, n)
+    cols = sum(v[:, :, :, a, :, :].mean(axis=2) for a in edges) / ne  # (4, Q, k', n')
     K2row = rows.reshape(4, p.n_Q, p.n) - K1[:, :, None]
     K2col = cols.reshape(4, p.n_Q, p.n) - K1[:, :, None]
+    if getattr(p, "kernel_level", 2) == 1:
+        K2row = np.zeros_like(K2row)
+        K2col = np.zeros_like(K2col)
     return K1, K2row, K2col
 
 

@@ -40,6 +40,8 @@ class Options(C.Structure):
         ("time_steps", C.c_int),
         ("q_chunk", C.c_int),
         ("assembly", C.c_int),
+        ("kernel_level", C.c_int),
+        ("edge_rule", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -174,6 +176,8 @@ class Solver:
         o.time_steps = 1 if time_steps else 0
         o.q_chunk = q_chunk
         o.assembly = assembly
+        o.kernel_level = p.kernel_level
+        o.edge_rule = {"both": 0, "lower": 1}[p.edge_rule]
         self._alloc = None
         if use_torch:
             import torch

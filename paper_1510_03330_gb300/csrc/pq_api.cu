@@ -369,6 +369,12 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     return fail(nullptr, PQ_EINVAL, "assembly must be 0 (tiled) or 1 (general)");
   }
   b.assembly = o.assembly;
+  if (o.kernel_level < 0 || o.kernel_level > 2 || o.edge_rule < 0 || o.edge_rule > 1) {
+    delete c;
+    return fail(nullptr, PQ_EINVAL, "kernel_level must be 0, 1 or 2 and edge_rule 0 or 1");
+  }
+  b.first_level = o.kernel_level == 1;
+  b.lower_edge = o.edge_rule == 1;
 
   if (pq::assemble_smem_bytes(g, c->c64) > 200 * 1024) {
     delete c;

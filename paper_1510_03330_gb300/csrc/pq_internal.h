@@ -59,6 +59,8 @@ struct Buffers {
   double2 *krow = nullptr;       // BF16x3: edge row sums of Phi accumulated by the BSE epilogue
   int vfmt = 0;
   int assembly = 0;              // BF16x3 assembly kernel: 0 tiled where the shape allows, 1 general
+  bool first_level = false;      // kernel approximation of the fill: K1 only (else K1 + K2)
+  bool lower_edge = false;       // K2 from the lower frequency edge alone (else the mean of both edges)
   int ld = 0;                    // row stride of gam and fv (elements)
   int q_chunk = 0;               // q-momenta assembled and multiplied per pass
   void *phi_new = nullptr;       // Jacobi target when the transfers run in several passes

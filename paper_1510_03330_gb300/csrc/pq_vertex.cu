@@ -54,17 +54,20 @@ struct EdgeSum<float2> {
 // K1[r][Q], K2row[r][k][Q], K2col[r][k'][Q]; one block per (Q, r).
 // ROWSUM: the row-edge sums of K2row come from krow ([r][k][Q], accumulated by the BSE
 // epilogue that wrote this Phi) instead of strided reads of Phi.
+// Ablations of Sec. II.A: lower_edge takes the lower frequency edge of the other leg alone
+// (K1: the corner at the lower edges of both legs); first_level keeps K1 only (K2 = 0).
 template <typename S, bool ROWSUM>
 __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__restrict__ k1,
                                double2 *__restrict__ k2row, double2 *__restrict__ k2col,
-                               const double2 *__restrict__ krow) {
+                               const double2 *__restrict__ krow, bool lower_edge, bool first_level) {
   __shared__ double2 red[256];
   __shared__ double2 sk1;
   const int Q = blockIdx.x, r = blockIdx.y;
   const long long n = g.n;
   const S *V = phi + ((long long)r * g.nQ + Q) * n * n;
   const int nn = g.n_nu, nk = g.nk;
-  const double inv = 1.0 / (2.0 * nk);
+  const int ne = lower_edge ? 1 : 2;  // frequency edges averaged
+  const double inv = 1.0 / ((double)ne * nk);
   double2 *K2r = k2row + (long long)r * g.n * g.nQ + Q, *K2c = k2col + (long long)r * g.n * g.nQ + Q;
   // edge means of the other leg (momentum averaged), kept until K1 is known; the first level
   // is their mean over the edge columns, i.e. over the four corners and all momentum pairs
@@ -84,9 +87,11 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
 #pragma unroll 8
       for (int b = 0; b < nk; ++b) {
         es_r.add(V[k * n + b * nn]);
-        es_r.add(V[k * n + b * nn + nn - 1]);
         es_c.add(V[(long long)(b * nn) * n + k]);
-        es_c.add(V[(long long)(b * nn + nn - 1) * n + k]);
+        if (!lower_edge) {
+          es_r.add(V[k * n + b * nn + nn - 1]);
+          es_c.add(V[(long long)(b * nn + nn - 1) * n + k]);
+        }
       }
       rs = es_r.get();
     }
@@ -94,7 +99,7 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
     K2r[(long long)k * g.nQ] = inv * rs;
     K2c[(long long)k * g.nQ] = inv * cs;
     const int f = k % nn;
-    if (f == 0 || f == nn - 1) acc = acc + cs;  // corners: edge rows x edge columns
+    if (f == 0 || (!lower_edge && f == nn - 1)) acc = acc + cs;  // corners: edge rows x edge columns
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -103,14 +108,15 @@ __global__ void kernels_kernel(Grid g, const S *__restrict__ phi, double2 *__res
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    sk1 = (1.0 / (4.0 * nk * nk)) * red[0];
+    sk1 = (1.0 / ((double)ne * ne * nk * nk)) * red[0];
     k1[(long long)r * g.nQ + Q] = sk1;
   }
   __syncthreads();
   const double2 K1 = sk1;
   for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
-    K2r[(long long)k * g.nQ] = K2r[(long long)k * g.nQ] - K1;
-    K2c[(long long)k * g.nQ] = K2c[(long long)k * g.nQ] - K1;
+    const double2 z = make_double2(0.0, 0.0);
+    K2r[(long long)k * g.nQ] = first_level ? z : K2r[(long long)k * g.nQ] - K1;
+    K2c[(long long)k * g.nQ] = first_level ? z : K2c[(long long)k * g.nQ] - K1;
   }
 }
 
@@ -354,12 +360,15 @@ size_t assemble_smem_bytes(const Grid &g, bool c64) {
 
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64, bool rowsums) {
   dim3 grid(g.nQ, 4);
-  if (c64 && rowsums)
-    kernels_kernel<float2, true><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, b.krow);
+  if (c64 && rowsums && !b.lower_edge)  // the products' row sums span both edges
+    kernels_kernel<float2, true><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, b.krow,
+                                                       false, b.first_level);
   else if (c64)
-    kernels_kernel<float2, false><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr);
+    kernels_kernel<float2, false><<<grid, 256, 0, st>>>(g, (const float2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr,
+                                                        b.lower_edge, b.first_level);
   else
-    kernels_kernel<double2, false><<<grid, 256, 0, st>>>(g, (const double2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr);
+    kernels_kernel<double2, false><<<grid, 256, 0, st>>>(g, (const double2 *)b.phi, b.k1, b.k2row, b.k2col, nullptr,
+                                                         b.lower_edge, b.first_level);
   return cudaGetLastError();
 }
 

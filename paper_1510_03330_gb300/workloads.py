@@ -43,6 +43,9 @@ class Params:
     tau_panels, tau_order, tau_matsubara   quadrature of the second-order
               self-energy: Gauss-Legendre panels on [0, beta], nodes per panel,
               and the Matsubara cut (n in [-M, M-1]) of the G(tau) sums.
+    kernel_level   2: the fill uses K1 + K2 (second level); 1: K1 only (Sec. II.A).
+    edge_rule      "both": K2 from the mean of the lower and upper frequency edges of
+              the other leg; "lower": the lower edge alone (Sec. II.A).
     """
 
     lattice: str
@@ -58,6 +61,8 @@ class Params:
     tau_panels: int = 64
     tau_order: int = 16
     tau_matsubara: int = 2048
+    kernel_level: int = 2
+    edge_rule: str = "both"
 
     @property
     def n_k(self) -> int:

@@ -77,6 +77,17 @@ def test_bad_q_chunk_is_rejected(lib):
     assert "q_chunk" in lib.pq_last_error(None).decode()
 
 
+@pytest.mark.parametrize("field,value,word", [("assembly", 2, "assembly"), ("kernel_level", 3, "kernel_level"),
+                                              ("edge_rule", 2, "edge_rule")])
+def test_bad_kernel_options_are_rejected(lib, field, value, word):
+    o = binding.default_options()
+    assert (o.assembly, o.kernel_level, o.edge_rule) == (0, 0, 0)
+    setattr(o, field, value)
+    h = C.c_void_p()
+    assert lib.pq_init(C.byref(h), 1, 2.0, 1.0, 0.0, 2, 8, 7, C.byref(o)) == binding.PQ_EINVAL
+    assert word in lib.pq_last_error(None).decode()
+
+
 def test_batch_arguments_are_checked_without_touching_the_gpu(lib):
     o = binding.BatchOptions()
     lib.pq_batch_default_options(C.byref(o))

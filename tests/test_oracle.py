@@ -174,6 +174,45 @@ def test_kernel_reconstruction_of_separable_vertex():
         assert np.abs(v - phi[x]).max() < 1e-13
 
 
+def test_kernel_ablations_lower_edge_and_first_level():
+    """The ablations of Sec. II.A.  (i) A separable Phi = a(Q) + b(Q,k) + c(Q,k') is
+    rebuilt exactly by the lower-edge rule too.  (ii) A Phi living only on the upper
+    frequency edge of the column leg (n' = n_hi, rows n > n_lo) has zero kernels under the
+    lower-edge rule (it never looks at that edge) and K2row = 1/2 of it under the two-edge
+    rule (the mean of the edges).  (iii) The first level keeps K1 and sets K2 = 0."""
+    base = SMALL_ODD
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((4, base.n_Q)) + 1j * rng.standard_normal((4, base.n_Q))
+    b = rng.standard_normal((4, base.n_Q, base.n)) + 1j * rng.standard_normal((4, base.n_Q, base.n))
+    c = rng.standard_normal((4, base.n_Q, base.n)) + 1j * rng.standard_normal((4, base.n_Q, base.n))
+    phi = a[:, :, None, None] + b[:, :, :, None] + c[:, :, None, :]
+    p = base.with_(edge_rule="lower")
+    g = O.make_grid(p)
+    K = O.extract_kernels(g, phi)
+    kk, kn, qk, qm = O.box_indices(g)
+    for x in range(4):
+        v = O.kernel_value(
+            g, K, x, (kk[None, :, None], kn[None, :, None]), (kk[None, None, :], kn[None, None, :]),
+            (qk[:, None, None], qm[:, None, None]))
+        assert np.abs(v - phi[x]).max() < 1e-13
+    # (ii) upper column edge only
+    nn = p.n_nu
+    f = np.arange(p.n) % nn
+    edge = np.zeros((4, p.n_Q, p.n, p.n), dtype=np.complex128)
+    edge[:, :, f > 0, :] = 1.0
+    edge[:, :, :, f != nn - 1] = 0.0
+    K1, K2r, K2c = O.extract_kernels(g, edge)
+    assert np.abs(K1).max() == 0 and np.abs(K2r).max() == 0 and np.abs(K2c).max() == 0
+    K1b, K2rb, K2cb = O.extract_kernels(O.make_grid(base), edge)
+    # two-edge rule: corners (n_hi, n_hi) of 4 -> K1 = 1/4; rows n > n_lo see one of two edges
+    assert np.allclose(K1b, 0.25)
+    assert np.allclose(K2rb[:, :, f > 0], 0.5 - 0.25) and np.allclose(K2rb[:, :, f == 0], -0.25)
+    # (iii) first level
+    K1f, K2rf, K2cf = O.extract_kernels(O.make_grid(base.with_(kernel_level=1)), phi)
+    K1s, _, _ = O.extract_kernels(O.make_grid(base), phi)
+    assert np.array_equal(K1f, K1s) and not K2rf.any() and not K2cf.any()
+
+
 # --------------------------------------------------------------------------- identities of the exact equations
 
 
