@@ -13,7 +13,7 @@ from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, Params, random_
 
 pytestmark = pytest.mark.gpu
 
-BASE = Params("square", beta=3.0, U=1.5, mu=0.1, L=4, n_nu=8, n_Omega=8)
+BASE = Params("square", beta=3.0, U=1.5, mu=0.1, L=2, n_nu=8, n_Omega=8)
 
 
 @pytest.fixture(scope="module", autouse=True)

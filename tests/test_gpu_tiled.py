@@ -19,6 +19,7 @@ SHAPES = {
     "L3_nu8": Params("square", beta=2.0, U=1.0, mu=0.3, L=3, n_nu=8, n_Omega=7, hop=0.8),  # G = 1, odd NOmega
     "bethe_nu12": Params("bethe", beta=4.0, U=1.0, mu=0.0, L=1, n_nu=12, n_Omega=9),  # nk = 1
     "L4_nu16": Params("square", beta=4.0, U=2.0, mu=0.0, L=4, n_nu=16, n_Omega=16),  # the bench block shape
+    "L4_nu4": Params("square", beta=3.0, U=1.5, mu=0.1, L=4, n_nu=4, n_Omega=4),     # G = 4 at oracle-friendly size
 }
 
 
@@ -68,7 +69,7 @@ def test_tiled_matches_general(name, q_chunk):
 def test_tiled_matches_oracle(q_chunk):
     from paper_1510_03330_gb300.binding import Solver
 
-    p = SHAPES["L4_nu8"]
+    p = SHAPES["L4_nu4"]
     st = O.zero_state(p)
     errs = {}
     with Solver(p, precision=SPLIT_BF16X3, q_chunk=q_chunk) as s:
