@@ -105,6 +105,10 @@ typedef struct {
    * lower and upper edges of the box; 1 the lower edge alone (the paper's example of
    * one edge), with K1 at the lower corner. */
   int edge_rule;
+  /* Self-energy: 0 (default) the regulated Schwinger-Dyson equation (Sec. II.B:
+   * Sigma~1 + Sigma~2 + the box sum of F - F~); 1 Eq. PA_Sigma summed on the vertex box
+   * with the vertex cut off at its boundary (zero outside the box), for comparison. */
+  int sde;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */

@@ -413,6 +413,22 @@ def sigma_delta_F(g: Grid, G: Propagator, F, K, lam, ks=None):
     return out
 
 
+def sigma_truncated(g: Grid, G: Propagator, F):
+    """Eq. PA_Sigma summed on the vertex box with the vertex cut off at its boundary,
+    the direct truncation that Sec. II.B regulates and Sec. III contrasts with:
+    -(U/4)(T/N)^2 sum_{k',q in box} [G(k+q)G(k'+q)G(k')(F_d - F_m) + G(q-k')G(q-k)G(k')(F_s + F_t)]
+    for every k of the box; zero for k outside it, where the truncated vertex vanishes."""
+    p = g.p
+    kk, kn, qk, qm = box_indices(g)
+    q3, k3, kp3 = qk[:, None, None], kk[None, :, None], kk[None, None, :]
+    m3, n3, np3 = qm[:, None, None], kn[None, :, None], kn[None, None, :]
+    ph, pp = sde_weights(g, G, k3, n3, kp3, np3, q3, m3)
+    tot = (ph * (F[D] - F[M]) + pp * (F[S] + F[T_])).sum(axis=(0, 2))  # over q and k'
+    out = np.zeros((g.nk, p.n_ext), dtype=np.complex128)
+    out[kk, kn - g.e_lo] = -(p.U / 4.0) * (g.T / g.nk) ** 2 * tot
+    return out
+
+
 def sigma2_kernel_terms(g: Grid, G: Propagator, K, outputs=None, chunk_elems=1 << 22):
     """Sigma~2 (Sec. II.B): Eq. PA_Sigma with F~ - Lambda^0, summed directly over
     k' and q on the box enlarged sigma2_factor times, for every k of the
@@ -533,10 +549,13 @@ def iterate(p, state: State, lam=None) -> IterationResult:
     X_ph, X_pp = bubbles(g, G)
     K = extract_kernels(g, state.phi)
     gamma, F = assemble(g, state.phi, K, lam)
-    s1 = sigma1_second_order(g, state.sigma)
-    s2 = sigma2_kernel_terms(g, G, K)
-    s3 = sigma_delta_F(g, G, F, K, lam)
-    sigma_new = s1 + s2 + s3
+    if getattr(p, "sde", "regulated") == "truncated":
+        sigma_new = sigma_truncated(g, G, F)
+    else:
+        s1 = sigma1_second_order(g, state.sigma)
+        s2 = sigma2_kernel_terms(g, G, K)
+        s3 = sigma_delta_F(g, G, F, K, lam)
+        sigma_new = s1 + s2 + s3
     phi_new = bse(gamma, F, X_ph, X_pp)
     a = p.mix
     nxt = State(a * phi_new + (1 - a) * state.phi, a * sigma_new + (1 - a) * state.sigma)

@@ -42,6 +42,7 @@ class Options(C.Structure):
         ("assembly", C.c_int),
         ("kernel_level", C.c_int),
         ("edge_rule", C.c_int),
+        ("sde", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -178,6 +179,7 @@ class Solver:
         o.assembly = assembly
         o.kernel_level = p.kernel_level
         o.edge_rule = {"both": 0, "lower": 1}[p.edge_rule]
+        o.sde = {"regulated": 0, "truncated": 1}[p.sde]
         self._alloc = None
         if use_torch:
             import torch

@@ -145,9 +145,14 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
   mark(2);
   CK(pq::launch_kernels_extract(st, g, b, c->c64, b.vfmt == pq::V_BF16P && c->krow_ok));
   mark(3);
-  CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
-  mark(4);
-  CK(pq::launch_sigma2(st, g, c->z, b));
+  if (b.truncated) {
+    mark(4);
+    CK(pq::launch_sigma_truncated(st, g, b));
+  } else {
+    CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
+    mark(4);
+    CK(pq::launch_sigma2(st, g, c->z, b));
+  }
   mark(5);
   const long long nn = g.n;
   const int np = num_passes(c);
@@ -373,6 +378,11 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     delete c;
     return fail(nullptr, PQ_EINVAL, "kernel_level must be 0, 1 or 2 and edge_rule 0 or 1");
   }
+  if (o.sde < 0 || o.sde > 1) {
+    delete c;
+    return fail(nullptr, PQ_EINVAL, "sde must be 0 (regulated) or 1 (truncated)");
+  }
+  b.truncated = o.sde == 1;
   b.first_level = o.kernel_level == 1;
   b.lower_edge = o.edge_rule == 1;
 
@@ -449,7 +459,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.gemm_work, cs * 64 * (size_t)g.nk * std::max(z.ntau, g.n_ext)},
   };
   b.gemm_work_elems = 64LL * g.nk * std::max(z.ntau, g.n_ext);
-  b.chi_part_elems = 4LL * b.q_chunk * g.n_om * ((g.n + 63) / 64);
+  // partial sums of chi per pass; also the bubble sums S_ph, S_pp of the truncated scheme
+  b.chi_part_elems = std::max(4LL * b.q_chunk * g.n_om * ((g.n + 63) / 64), 2LL * g.nQ);
   size_t need = 0;
   for (auto &r : reqs) need += (r.bytes + 255) & ~(size_t)255;
   for (auto &r : reqs) {

@@ -61,6 +61,7 @@ struct Buffers {
   int assembly = 0;              // BF16x3 assembly kernel: 0 tiled where the shape allows, 1 general
   bool first_level = false;      // kernel approximation of the fill: K1 only (else K1 + K2)
   bool lower_edge = false;       // K2 from the lower frequency edge alone (else the mean of both edges)
+  bool truncated = false;        // Sigma from Eq. PA_Sigma on the box alone (else the regulated Sigma)
   int ld = 0;                    // row stride of gam and fv (elements)
   int q_chunk = 0;               // q-momenta assembled and multiplied per pass
   void *phi_new = nullptr;       // Jacobi target when the transfers run in several passes
@@ -114,6 +115,8 @@ cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int n
 // vertex steps (pq_vertex.cu)
 // K1/K2 from the state; with rowsums, K2row from the edge row sums the last BSE accumulated
 cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, bool c64, bool rowsums = false);
+// truncated scheme: Sigma~1 <- 0, Sigma~2 <- the Lambda^0 part of the box sum (pq_onebody.cu)
+cudaError_t launch_sigma_truncated(cudaStream_t st, const Grid &g, Buffers &b);
 cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const double *lam4, const Pass &p);
 struct Lam;
 // tiled BF16 assembly (pq_assemble_tiled.cu): false / cudaErrorInvalidValue where the shape

@@ -276,6 +276,57 @@ __global__ void chi_sum_kernel(Grid g, int qb, int nq, int nchunk, const double2
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Truncated Schwinger-Dyson scheme (the ablation of the regulated Sigma, Sec. II.B): Eq.
+// PA_Sigma on the box with the vertex cut off there.  Its F - Lambda^0 part is the box sum the
+// assembly accumulates; the Lambda^0 = (U, -U, 2U, 0) part factorises through the bubbles:
+//   -(U/4)(T/N)^2 2U sum_{k',q in box} [G(k+q) G(k'+q) G(k') + G(q-k') G(q-k) G(k')]
+//     = -(U^2/2)(T/N) sum_Q [G(k+q) S_ph(Q) + G(q-k) S_pp(Q)],   S_x(Q) = sum_{k' in box} X_x(Q,k'),
+// for k in the box; zero outside it.  One block per Q for the row sums, then one thread per output.
+__global__ void box_bubble_sums(Grid g, const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
+                                double2 *__restrict__ sph, double2 *__restrict__ spp) {
+  __shared__ double2 ra[256], rb[256];
+  const int Q = blockIdx.x;
+  double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+  for (int k = threadIdx.x; k < g.n; k += blockDim.x) {
+    a = a + xph[(long long)Q * g.n + k];
+    b = b + xpp[(long long)Q * g.n + k];
+  }
+  ra[threadIdx.x] = a;
+  rb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      ra[threadIdx.x] = ra[threadIdx.x] + ra[threadIdx.x + w];
+      rb[threadIdx.x] = rb[threadIdx.x] + rb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sph[Q] = ra[0];
+    spp[Q] = rb[0];
+  }
+}
+
+__global__ void sigma_box_lambda0(Grid g, const double2 *__restrict__ gtab, const double2 *__restrict__ sph,
+                                  const double2 *__restrict__ spp, double2 *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nk * g.n_ext) return;
+  const int ik = i / g.n_ext, n = g.e_lo + i % g.n_ext;
+  double2 s = make_double2(0.0, 0.0);
+  if (n >= g.n_lo && n <= g.n_hi) {
+    for (int Q = 0; Q < g.nQ; ++Q) {
+      const int iq = Q / g.n_om, m = g.m_lo + Q % g.n_om;
+      const double2 gkq = gtab[(long long)kadd(g, ik, iq) * g.n_g + (n + m - g.g_lo)];
+      const double2 gqk = gtab[(long long)ksub(g, iq, ik) * g.n_g + (m - n - 1 - g.g_lo)];
+      s = cfma(gkq, sph[Q], cfma(gqk, spp[Q], s));
+    }
+    s = (-0.5 * g.U * g.U * g.T / g.nk) * s;
+  }
+  out[i] = s;
+}
+
+
+
 }  // namespace
 
 cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b) {
@@ -333,6 +384,17 @@ cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const 
   e = zgemm_fp64_splitk(st, g.nk, g.n_ext, g.nk, one, a.phc, g.nk, a.srn, g.n_ext, zero, a.out, g.n_ext, a.work,
                         a.work_elems);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_truncated(cudaStream_t st, const Grid &g, Buffers &b) {
+  // S_ph, S_pp in the chi partial-sum scratch (4 N_Q n / CHI_ROWS >= 2 N_Q entries)
+  if (b.chi_part_elems < 2LL * g.nQ) return cudaErrorInvalidValue;
+  double2 *sph = b.chi_part, *spp = b.chi_part + g.nQ;
+  cudaError_t e = cudaMemsetAsync(b.sigma1, 0, sizeof(double2) * (size_t)g.nk * g.n_ext, st);
+  if (e != cudaSuccess) return e;
+  box_bubble_sums<<<g.nQ, 256, 0, st>>>(g, b.xph, b.xpp, sph, spp);
+  sigma_box_lambda0<<<nblk((long long)g.nk * g.n_ext, 256), 256, 0, st>>>(g, b.gtab, sph, spp, b.sigma2);
   return cudaGetLastError();
 }
 

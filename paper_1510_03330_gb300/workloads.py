@@ -46,6 +46,8 @@ class Params:
     kernel_level   2: the fill uses K1 + K2 (second level); 1: K1 only (Sec. II.A).
     edge_rule      "both": K2 from the mean of the lower and upper frequency edges of
               the other leg; "lower": the lower edge alone (Sec. II.A).
+    sde       "regulated": Sigma = Sigma~1 + Sigma~2 + the box sum of F - F~ (Sec. II.B);
+              "truncated": Eq. PA_Sigma on the box with the vertex cut off there.
     """
 
     lattice: str
@@ -63,6 +65,7 @@ class Params:
     tau_matsubara: int = 2048
     kernel_level: int = 2
     edge_rule: str = "both"
+    sde: str = "regulated"
 
     @property
     def n_k(self) -> int:

@@ -78,10 +78,10 @@ def test_bad_q_chunk_is_rejected(lib):
 
 
 @pytest.mark.parametrize("field,value,word", [("assembly", 2, "assembly"), ("kernel_level", 3, "kernel_level"),
-                                              ("edge_rule", 2, "edge_rule")])
+                                              ("edge_rule", 2, "edge_rule"), ("sde", 2, "sde")])
 def test_bad_kernel_options_are_rejected(lib, field, value, word):
     o = binding.default_options()
-    assert (o.assembly, o.kernel_level, o.edge_rule) == (0, 0, 0)
+    assert (o.assembly, o.kernel_level, o.edge_rule, o.sde) == (0, 0, 0, 0)
     setattr(o, field, value)
     h = C.c_void_p()
     assert lib.pq_init(C.byref(h), 1, 2.0, 1.0, 0.0, 2, 8, 7, C.byref(o)) == binding.PQ_EINVAL

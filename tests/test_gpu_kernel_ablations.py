@@ -1,6 +1,7 @@
-"""GPU parity of the kernel-approximation ablations of Sec. II.A (pq_options.kernel_level,
-pq_options.edge_rule): the first-level fill (K1 only) and second-level kernels read at the
-lower frequency edge alone.  From one synthetic state with stripes (so that the rules
+"""GPU parity of the ablations the paper argues from: the kernel approximation of Sec. II.A
+(pq_options.kernel_level, pq_options.edge_rule: the first-level fill, K1 only, and
+second-level kernels read at the lower frequency edge alone) and the self-energy of Sec.
+II.B (pq_options.sde: Eq. PA_Sigma truncated to the box instead of the regulated sum).  From one synthetic state with stripes (so that the rules
 differ), one iteration on the GPU against the FP64 oracle with the same Params, in the
 FP64 path (1e-10) and on the BF16x3 path (whose products also sum the row edges for the
 next iteration: the lower-edge rule must not use them); a second iteration checks the
@@ -37,7 +38,7 @@ def all_phi(s, p):
 
 @pytest.mark.parametrize("precision,tol,tol_phi", [(FP64, 1e-10, 1e-10), (SPLIT_BF16X3, 5e-5, 3e-4)])
 @pytest.mark.parametrize("variant", [dict(kernel_level=1), dict(edge_rule="lower"),
-                                     dict(kernel_level=1, edge_rule="lower")])
+                                     dict(kernel_level=1, edge_rule="lower"), dict(sde="truncated")])
 def test_kernel_ablation_matches_oracle(precision, tol, tol_phi, variant):
     from paper_1510_03330_gb300.binding import Solver
 

@@ -213,6 +213,28 @@ def test_kernel_ablations_lower_edge_and_first_level():
     assert np.array_equal(K1f, K1s) and not K2rf.any() and not K2cf.any()
 
 
+def test_truncated_sde_approaches_second_order_as_the_box_grows():
+    """The truncated Schwinger-Dyson sum (Eq. PA_Sigma on the box, vertex cut off) at the
+    first iteration, where F = Lambda^0, is the second-order self-energy restricted to the
+    box; as the box grows it must approach Sigma~1 (pinned by its closed forms), with the
+    truncation error falling like the GGG tail, about 1/Nnu^2.  A wrong prefactor or sign
+    converges to a multiple of Sigma~1 instead."""
+    devs = []
+    for nu in (8, 16, 32):
+        p = Params("bethe", beta=2.0, U=1.0, mu=0.0, L=1, n_nu=nu, n_Omega=nu - 1, sde="truncated")
+        g = O.make_grid(p)
+        res = O.iterate(p, O.zero_state(p))
+        s1 = O.sigma1_second_order(g, np.zeros((1, p.n_ext), np.complex128))
+        kk, kn, qk, qm = O.box_indices(g)
+        lo = kn[(kn >= -2) & (kn <= 1)] - g.e_lo
+        devs.append(np.abs(res.sigma_new[0, lo] - s1[0, lo]).max() / np.abs(s1[0, lo]).max())
+        outside = np.ones(p.n_ext, bool)
+        outside[kn - g.e_lo] = False
+        assert not res.sigma_new[0, outside].any()  # zero where the truncated vertex vanishes
+    assert devs[0] / devs[1] > 3 and devs[1] / devs[2] > 3, devs
+    assert devs[2] < 2e-3, devs
+
+
 # --------------------------------------------------------------------------- identities of the exact equations
 
 
