@@ -160,23 +160,8 @@ __global__ void sigma_update_kernel(Grid g, const double2 *__restrict__ s1, cons
   }
 }
 
-// Element e of the F operand buffer as a double2: one complex of the storage type,
-// or the sum of the three BF16 pieces of the planes (Re h, Im h, Re l, Im l, Re r, Im r).
-template <int FMT>
-__device__ inline double2 f_elem(const void *fv, long long ps, long long e) {
-  if constexpr (FMT == V_C128) {
-    return ((const double2 *)fv)[e];
-  } else if constexpr (FMT == V_C64) {
-    const float2 v = ((const float2 *)fv)[e];
-    return make_double2(v.x, v.y);
-  } else {
-    const __nv_bfloat16 *p = (const __nv_bfloat16 *)fv;
-    return make_double2((double)__bfloat162float(p[e]) + (double)__bfloat162float(p[2 * ps + e]) +
-                            (double)__bfloat162float(p[4 * ps + e]),
-                        (double)__bfloat162float(p[ps + e]) + (double)__bfloat162float(p[3 * ps + e]) +
-                            (double)__bfloat162float(p[5 * ps + e]));
-  }
-}
+// Element e of the F operand buffer of the FP64 path.
+__device__ inline double2 f_elem64(const void *fv, long long e) { return ((const double2 *)fv)[e]; }
 
 // Element e of the F operand buffer of a split path in FP32: the complex64 value, or the sum
 // of the three BF16 pieces (h + l is exact; adding r rounds once, at 2^-24 relative).
@@ -232,7 +217,7 @@ __global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, 
     double2 rs;
     if constexpr (FMT == V_C128) {
       rs = make_double2(0.0, 0.0);
-      for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem<FMT>(fv, ps, base + (long long)k * ld + kp), X[kp], rs);
+      for (int kp = lane; kp < g.n; kp += 32) rs = cfma(f_elem64(fv, base + (long long)k * ld + kp), X[kp], rs);
       for (int o = 16; o > 0; o >>= 1)
         rs = make_double2(rs.x + __shfl_xor_sync(0xffffffffu, rs.x, o), rs.y + __shfl_xor_sync(0xffffffffu, rs.y, o));
     } else {
