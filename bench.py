@@ -61,6 +61,35 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def library_gemm_tflops(torch, kind):
+    """Dense GEMM rate of the vendor library on this GPU (torch.matmul, i.e. cuBLAS), timed with
+    CUDA events: the measured peak for the FP64 products ("fp64": DGEMM, n = 4096) and for the
+    TF32 products ("tf32": FP32 GEMM on the TF32 tensor cores, n = 8192); the bf16 peak is
+    MEASURED_PEAKS.json's."""
+    n, dt, tf32, reps = (4096, torch.float64, False, 3) if kind == "fp64" else (8192, torch.float32, True, 20)
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        x = torch.randn(n, n, dtype=dt, device="cuda")
+        y = torch.randn(n, n, dtype=dt, device="cuda")
+        z = torch.empty(n, n, dtype=dt, device="cuda")
+        for _ in range(2):
+            torch.matmul(x, y, out=z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(x, y, out=z)
+        e1.record()
+        torch.cuda.synchronize()
+        tflops = 2.0 * n**3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del x, y, z
+        return tflops
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+        torch.cuda.empty_cache()
+
+
 def describe(name, p, precision):
     return {
         "workload": f"{name}: {p.lattice} lattice {p.L}x{p.L} k, Nnu={p.n_nu}, NOmega={p.n_Omega}, U={p.U}, "
@@ -434,6 +463,11 @@ def main():
         return {"iterations": 2, "sigma_rel_err": relerr(sol.sigma(), ref_sig),
                 "F_m_rel_err": relerr(sol.F(1, p.n_Q // 2), ref_F), "chi_m_rel_err": relerr(sol.chi(1), ref_chi)}
 
+    lib_peaks = {"dgemm_tflops": library_gemm_tflops(torch, "fp64"),
+                 "tf32_gemm_tflops": library_gemm_tflops(torch, "tf32"),
+                 "source": "cuBLAS through torch.matmul, timed live on this GPU"}
+    if compare is not None:
+        compare["fp64_frac_of_measured_dgemm"] = compare["fp64_bse_tflops"] / lib_peaks["dgemm_tflops"]
     solver = Solver(p, precision=a.precision, time_steps=True, q_chunk=a.q_chunk)
     if compare is not None and not compare.get("extrapolated"):
         solver.iterate(2)
@@ -480,12 +514,16 @@ def main():
     bse_tflops = bse_flops / (steps["bse"] * 1e-3) / 1e12
     remap_gbs = remap_bytes / (steps["assemble"] * 1e-3) / 1e9
     if a.precision == FP64:
-        bse_roof = {"bound": "alu", "achieved": bse_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                    "frac": bse_tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
-                    "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+        bse_roof = {"bound": "alu", "achieved": bse_tflops, "peak": lib_peaks["dgemm_tflops"], "unit": "TFLOP/s",
+                    "frac": bse_tflops / lib_peaks["dgemm_tflops"], "traffic": None,
+                    "peak_source": "cuBLAS DGEMM measured live (FP64 pipe)",
+                    "frac_of_nominal": bse_tflops / FP64_NOMINAL_TFLOPS}
     else:
-        ratio = {SPLIT_TF32X3: 1.1 / 2.25, SPLIT_BF16X3: 1.0, SPLIT_BF16X6: 1.0}[a.precision]
-        peak = pk["bf16_tflops"] * ratio
+        if a.precision == SPLIT_TF32X3:
+            ratio, peak, psrc = None, lib_peaks["tf32_gemm_tflops"], "cuBLAS TF32 GEMM measured live"
+        else:
+            ratio = 1.0
+            peak, psrc = pk["bf16_tflops"] * ratio, f"{src} bf16 burst"
         # DRAM bytes per launch as a multiple of the algorithmic 32 n^2 bytes per GEMM (read A,
         # B, Phi; write Phi)
         tr, tsrc = full_tr.get("bse"), "ncu capture of this launch at full size"
@@ -495,7 +533,7 @@ def main():
                     "frac": bse_tflops / peak, "traffic": tr * 32.0 * n * n * 4 * nQ if tr else None,
                     "traffic_source": tsrc if tr else None,
                     "executed_tensor_frac": 3.0 * bse_tflops / peak,
-                    "peak_source": f"{src} bf16 burst x nominal ratio {ratio:.3f}"}
+                    "peak_source": psrc}
     tr = full_tr.get("assemble")
     remap_roof = {"bound": "hbm", "achieved": remap_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                   "frac": remap_gbs / pk["hbm_gbs"], "traffic": tr * remap_bytes if tr else None,
@@ -509,7 +547,8 @@ def main():
             "vs_baseline": None, "dtype": DTYPE[a.precision],
             "data": "synthetic", "config": cfg, "roofline": roof,
             "kernels": {"ms_per_iter": steps, "bse": bse_roof, "assemble": remap_roof},
-            "bse_tflops": bse_tflops, "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
+            "bse_tflops": bse_tflops, "measured_library_peaks": lib_peaks,
+            "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
             "device_bytes": dev_bytes}
     if compare is not None:
         compare["split_over_fp64"] = value / compare["fp64_iter_per_s"]
@@ -538,6 +577,10 @@ def main():
             alt.update({"iter_per_s": a.steps / (alt_ms / 1e3),
                         "bse_tflops": bse_flops / (bse_ms / a.steps * 1e-3) / 1e12,
                         "over_fp64": (a.steps / (alt_ms / 1e3)) / compare["fp64_iter_per_s"]})
+            alt_peak = lib_peaks["tf32_gemm_tflops"] if alt_prec == SPLIT_TF32X3 else pk["bf16_tflops"]
+            alt["bse_frac"] = alt["bse_tflops"] / alt_peak
+            alt["executed_tensor_frac"] = 3.0 * alt["bse_tflops"] / alt_peak
+            alt["peak_source"] = "cuBLAS TF32 GEMM measured live" if alt_prec == SPLIT_TF32X3 else f"{src} bf16 burst"
             line[alt_prec] = alt
 
     if not a.no_e2e:
