@@ -39,10 +39,11 @@ DEFAULT_WORKLOAD = "square8_u2_b4"
 DEFAULT_PRECISION = SPLIT_BF16X3
 DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulate)",
          SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
-# DRAM bytes of one launch / algorithmic bytes.  Measured at full size (one-pass ncu capture
-# of the launch itself, profiles/dram_square8_u2_b4_bf16x3.md) for the workload and scheme
-# it was taken on; otherwise from a capture on the 4x4 lattice scaled by the launch's size
-# (profiles/bse_split_tf32x3_square4_u2_b5.md); kernels changed since a capture have none.
+# DRAM bytes of one launch / algorithmic bytes (ncu dram__bytes_read + dram__bytes_write).
+# Measured at full size by a one-pass capture of the launch itself for the workload and scheme
+# it was taken on (8x8 BF16x3: products 166.5 GB, assembly 146.2 GB); otherwise from a capture
+# of the TF32x3 products on the 4x4 lattice, scaled by the launch's size; kernels changed since
+# a capture have none.
 FULL_TRAFFIC = {("square8_u2_b4", SPLIT_BF16X3): {"bse": 1.212, "assemble": 1.216}}
 BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
