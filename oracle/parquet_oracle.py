@@ -34,10 +34,14 @@ the design notes):
   * Sigma beyond its stored range is c1/(i nu) with c1 = -<nu Im Sigma> at the
     two outer stored frequencies (momentum averaged).
   * Jacobi update from the state (Phi, Sigma), linear mixing of both.
+  * Ablations of Sec. II.A/B selected by Params: kernel_level 1 keeps K1 only;
+    edge_rule "lower" reads K2 at the lower frequency edge alone (K1 at the lower
+    corner); sde "truncated" sums Eq. PA_Sigma on the box with the vertex cut off
+    there (Sigma = 0 outside the box).
 
-Parity unpinned: chi_s and chi_t (the pp-channel susceptibilities have no
-closed form or printed value to check against; chi_d and chi_m are pinned by
-the first-order RPA expansion).
+Every function is pinned by the tests (closed forms, limits, invariants, stored
+closed-form values); chi in all four channels by its first-order expansion at
+the first-iteration vertex.
 
 Array layout: Phi[r, Q, k, k'] with r in (d, m, s, t), Q = iq*NOmega + (m-m_lo),
 k = ik*Nnu + (n-n_lo); Sigma[ik, n-e_lo] on the extended range.

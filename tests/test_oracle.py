@@ -450,9 +450,11 @@ def test_third_order_survives_away_from_half_filling():
 
 
 def test_susceptibility_first_order_rpa():
-    """With the first-iteration vertex F = Lambda = (U, -U, ...), chi_m = chi0 + U chi0^2 and
+    """With the first-iteration vertex F = Lambda = (U, -U, 2U, 0), chi_m = chi0 + U chi0^2 and
     chi_d = chi0 - U chi0^2: the first-order terms of the RPA forms chi0/(1 -+ U chi0),
-    with chi0 = -(T/N) sum_k G0(k) G0(k+q) summed here with the test's own G0."""
+    with chi0 = -(T/N) sum_k G0(k) G0(k+q) summed here with the test's own G0; in the
+    particle-particle channels, with chi0pp = -(T/N) sum_k G0(k) G0(q-k),
+    chi_s = chi0pp - 2U chi0pp^2 and chi_t = chi0pp (F_t = 0)."""
     p = SMALL_ODD
     res = O.iterate(p, O.zero_state(p))
     chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
@@ -462,16 +464,20 @@ def test_susceptibility_first_order_rpa():
         qx, qy = divmod(iq, L)
         for im in range(p.n_Omega):
             m = m_lo + im
-            b = 0.0
+            b = bpp = 0.0
             for ik in range(N):
                 kx, ky = divmod(ik, L)
                 for n in range(n_lo, n_lo + p.n_nu):
-                    b += _g0_square(p, 2 * np.pi * kx / L, 2 * np.pi * ky / L, n) * _g0_square(
-                        p, 2 * np.pi * (kx + qx) / L, 2 * np.pi * (ky + qy) / L, n + m)
-            chi0 = -T / N * b
+                    gk = _g0_square(p, 2 * np.pi * kx / L, 2 * np.pi * ky / L, n)
+                    b += gk * _g0_square(p, 2 * np.pi * (kx + qx) / L, 2 * np.pi * (ky + qy) / L, n + m)
+                    # q - k: bosonic m minus fermionic n is the fermionic index m - n - 1
+                    bpp += gk * _g0_square(p, 2 * np.pi * (qx - kx) / L, 2 * np.pi * (qy - ky) / L, m - n - 1)
+            chi0, chi0pp = -T / N * b, -T / N * bpp
             Q = iq * p.n_Omega + im
             assert abs(chi[1, Q] - (chi0 + p.U * chi0**2)) < 1e-13
             assert abs(chi[0, Q] - (chi0 - p.U * chi0**2)) < 1e-13
+            assert abs(chi[2, Q] - (chi0pp - 2 * p.U * chi0pp**2)) < 1e-13
+            assert abs(chi[3, Q] - chi0pp) < 1e-13
 
 
 # --------------------------------------------------------------------------- tabulated Lambda
