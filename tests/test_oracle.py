@@ -235,6 +235,28 @@ def test_truncated_sde_approaches_second_order_as_the_box_grows():
     assert devs[2] < 2e-3, devs
 
 
+def test_first_level_equals_second_level_until_stripes_appear():
+    """From Phi = 0 the first iterate is constant in (k, k') (Sec. II.A), so its K2 vanishes
+    and the first- and second-level fills agree exactly for two iterations; the stripes of
+    the second iterate make them differ from the third on."""
+    a, b = O.zero_state(SMALL), O.zero_state(SMALL)
+    p1 = SMALL.with_(kernel_level=1)
+    for _ in range(2):
+        a, b = O.iterate(SMALL, a).state, O.iterate(p1, b).state
+    assert np.array_equal(a.sigma, b.sigma) and np.array_equal(a.phi, b.phi)
+    assert np.abs(O.iterate(SMALL, a).sigma_new - O.iterate(p1, b).sigma_new).max() > 1e-4
+
+
+def test_truncated_sde_keeps_particle_hole_symmetry():
+    """The truncated sum on a box symmetric under nu -> -nu keeps Re Sigma = 0 for the
+    half-filled Bethe lattice (odd NOmega: symmetric bosonic box)."""
+    p = BETHE_SMALL.with_(sde="truncated")
+    st = O.zero_state(p)
+    for _ in range(3):
+        st = O.iterate(p, st).state
+    assert np.abs(st.sigma.real).max() <= 1e-13 * np.abs(st.sigma).max()
+
+
 # --------------------------------------------------------------------------- identities of the exact equations
 
 
