@@ -72,6 +72,30 @@ def first_iteration_square(L=2, beta=3.0, U=1.5, mu=0.0, t=1.0, n_nu=8, n_omega=
     return rows
 
 
+def second_order_square(L=3, beta=2.0, U=1.1, mu=0.15, t=0.8, n_nu=6, n_omega=5):
+    """Second-order self-energy of the free square lattice (Sec. II.B: Sigma~1, and the regulated
+    Sigma of the first iteration from Phi = 0) with Fermi functions:
+    Sigma(k, i nu) = (U^2/N^2) sum_{a,b} [(1-f_a)(1-f_b) f_c + f_a f_b (1-f_c)] / (i nu - e_a - e_b + e_c),
+    c = a + b - k, e = eps - mu, on the extended range e in [m_lo + n_lo, m_hi + n_hi]."""
+    N = L * L
+    ks = [(x, y) for x in range(L) for y in range(L)]
+    e = np.array([-2 * t * (np.cos(2 * np.pi * x / L) + np.cos(2 * np.pi * y / L)) - mu for x, y in ks])
+    f = fermi(e, beta)
+    nlo, mlo = -n_nu // 2, -(n_omega // 2)
+    ns = np.arange(mlo + nlo, mlo + n_omega - 1 + nlo + n_nu)
+    nu = (2 * ns + 1) * np.pi / beta
+    rows = []
+    for ik, (kx, ky) in enumerate(ks):
+        s = np.zeros(ns.size, dtype=complex)
+        for ia, (ax, ay) in enumerate(ks):
+            for ib, (bx, by) in enumerate(ks):
+                ic = ((ax + bx - kx) % L) * L + (ay + by - ky) % L
+                s += ((1 - f[ia]) * (1 - f[ib]) * f[ic] + f[ia] * f[ib] * (1 - f[ic])) / (1j * nu - e[ia] - e[ib] + e[ic])
+        s *= U * U / N**2
+        rows += [(ik, int(n), v.real, v.imag) for n, v in zip(ns, s)]
+    return rows
+
+
 def write(name, header, rows):
     with open(os.path.join(HERE, name), "w") as f:
         for line in header:
@@ -92,6 +116,18 @@ def main():
            "Nnu = NOmega = 8: Phi_d = Phi_m = U^2 (T/N) sum G0 G0(k''+q), Phi_s = -2 U^2 (T/N) sum G0 G0(q-k''),",
            "Phi_t = 0, constant in (k, k').  Columns: Q = q-index * NOmega + (m - m_lo), Re Phi_d, Im Phi_d, Re Phi_s, Im Phi_s."],
           [(Q, d.real, d.imag, s.real, s.imag) for Q, d, s in rows])
+    rows = first_iteration_square(L=3, beta=2.0, U=1.1, mu=0.15, t=0.8, n_nu=6, n_omega=5)
+    write("first_iteration_square3_b2_u1p1_mu0p15.txt",
+          ["Worked first iteration of Sec. II.A on the 3x3 square lattice, t = 0.8, beta = 2, U = 1.1, mu = 0.15,",
+           "Nnu = 6, NOmega = 5 (same formulas as the 2x2 file; on 3x3, k + q and k - q are different points).",
+           "Columns: Q = q-index * NOmega + (m - m_lo), Re Phi_d, Im Phi_d, Re Phi_s, Im Phi_s."],
+          [(Q, d.real, d.imag, s.real, s.imag) for Q, d, s in rows])
+    write("second_order_square3_b2_u1p1_mu0p15.txt",
+          ["Second-order self-energy of the free 3x3 square lattice, t = 0.8, beta = 2, U = 1.1, mu = 0.15,",
+           "Nnu = 6, NOmega = 5: (U^2/N^2) sum_{a,b} [(1-f_a)(1-f_b) f_c + f_a f_b (1-f_c)]/(i nu - e_a - e_b + e_c),",
+           "c = a + b - k (Sec. II.B: Sigma~1, the regulated Sigma of the first iteration from Phi = 0).",
+           "Columns: k-index (ix * L + iy), n, Re Sigma, Im Sigma."],
+          second_order_square())
 
 
 if __name__ == "__main__":
