@@ -30,25 +30,28 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1510_03330_gb300.workloads import (CONFIGS, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_TF32X3,  # noqa: E402
-                                              batch_draw, device_bytes_bf16x3)
+from paper_1510_03330_gb300.workloads import (CONFIGS, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_FP16X3,  # noqa: E402
+                                              SPLIT_TF32X3, batch_draw, device_bytes_planes)
 
 METRIC = "parquet iter/s and BSE TFLOP/s: split-precision vs FP64 path at a stated Σ error"
 UNIT = "iter/s"
 DEFAULT_WORKLOAD = "square8_u2_b4"
-DEFAULT_PRECISION = SPLIT_BF16X3
+DEFAULT_PRECISION = SPLIT_FP16X3
 DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulate)",
-         SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate)", SPLIT_BF16X6: "bf16x6"}
+         SPLIT_BF16X3: "bf16x3 (split BF16 operands, fp32 accumulate in chunks)",
+         SPLIT_FP16X3: "fp16x3 (split FP16 operands, power-of-two scaled per channel, fp32 accumulate in chunks)",
+         SPLIT_BF16X6: "bf16x6"}
+PLANES = (SPLIT_BF16X3, SPLIT_FP16X3)
 # DRAM bytes of one launch / algorithmic bytes (ncu dram__bytes_read + dram__bytes_write).
 # Measured at full size by a one-pass capture of the launch itself for the workload and scheme
 # it was taken on (8x8 BF16x3: products 166.5 GB, assembly 146.2 GB); otherwise from a capture
 # of the TF32x3 products on the 4x4 lattice, scaled by the launch's size; kernels changed since
 # a capture have none.
-FULL_TRAFFIC = {("square8_u2_b4", SPLIT_BF16X3): {"bse": 1.212, "assemble": 1.216}}
+FULL_TRAFFIC = {}
 BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (8: tables, their prefix sums, two output passes), parquet assembly (1),
-# Sigma update (1), BSE (1)
+# Sigma update (1), BSE (1); FP16 planes add the kernel of the operand scales (1)
 LAUNCHES_PER_ITER = 22
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, nominal
 
@@ -221,7 +224,27 @@ def blas_threads():
 
         return max(i.get("num_threads", 1) for i in threadpool_info())
     except Exception:
-        return os.cpu_count() or 1
+        return int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+
+
+def oracle_baseline(workload, target_s=12.0):
+    """The oracle on its bounded sample twice: with the BLAS threads the host offers (numpy's
+    element-wise work runs on one thread either way, only the products of the sample use
+    several) and on one core (a child process with one BLAS thread)."""
+    p = CONFIGS[workload]
+    v, sample, secs = oracle_sample(p, target_s)
+    multi = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+             "sample": sample, "threads_note": "BLAS threads for the matrix products of the sample; "
+                                               "the element-wise numpy work is single-threaded"}
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample-only", workload,
+                        "--oracle-seconds", str(target_s)], env=env, capture_output=True, text=True)
+    try:
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        multi["one_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
+    except Exception:
+        multi["one_core"] = {"value": None, "error": (r.stderr or r.stdout)[-300:]}
+    return multi, secs
 
 
 # ----------------------------------------------------------------------------- main
@@ -246,11 +269,11 @@ def job_rate(units_per_rank, world, elapsed_s):
 BATCH = "batch64_seed1510"
 
 
-def pack_waves(draw, budget):
+def pack_waves(draw, budget, precision=SPLIT_FP16X3):
     """First-fit decreasing packing of the solves into waves of at most budget device bytes."""
     waves = []
-    for i in sorted(range(len(draw)), key=lambda i: -device_bytes_bf16x3(draw[i])):
-        b = device_bytes_bf16x3(draw[i])
+    for i in sorted(range(len(draw)), key=lambda i: -device_bytes_planes(draw[i], precision)):
+        b = device_bytes_planes(draw[i], precision)
         for w in waves:
             if w[1] + b <= budget:
                 w[0].append(i)
@@ -271,7 +294,8 @@ def run_batch(a, world, barrier, clk_factory):
     draw = batch_draw(1510, 64)
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
-    waves = pack_waves(draw, free - (8 << 30))
+    prec = a.precision if a.precision in PLANES else SPLIT_FP16X3
+    waves = pack_waves(draw, free - (8 << 30), prec)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     seq_ms = bat_ms = bse_ms = 0.0
@@ -279,7 +303,7 @@ def run_batch(a, world, barrier, clk_factory):
     clk = clk_factory()
     clk.start()
     for w in waves:
-        sols = [Solver(draw[i], precision=SPLIT_BF16X3, q_chunk=draw[i].n_k) for i in w]
+        sols = [Solver(draw[i], precision=prec, q_chunk=draw[i].n_k) for i in w]
         for s_ in sols:
             s_.iterate(1)
         torch.cuda.synchronize()
@@ -326,16 +350,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(CONFIGS) + [BATCH])
     ap.add_argument("--precision", default=DEFAULT_PRECISION,
-                    choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_BF16X6])
+                    choices=[FP64, SPLIT_TF32X3, SPLIT_BF16X3, SPLIT_FP16X3, SPLIT_BF16X6])
     ap.add_argument("--q-chunk", type=int, default=0,
                     help="q-momenta per pass of the iteration (0: all that fit in device memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample-only", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64 run that states the split path's error and the FP64 iteration rate")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
+    if a.oracle_sample_only:
+        v, sample, _ = oracle_sample(CONFIGS[a.oracle_sample_only], a.oracle_seconds)
+        print(json.dumps({"value": v, "sample": sample}), flush=True)
+        return 0
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,7 +374,7 @@ def main():
         p = None
         cfg = {"workload": "64 square-lattice Hubbard solves drawn with seed 1510 (numpy PCG64): L in 2..6, "
                            "Nnu in {8,16,24,32}, NOmega = Nnu, U in [0.5, 3], beta in [2, 10], half filling",
-               "precision": SPLIT_BF16X3,
+               "precision": a.precision if a.precision in PLANES else SPLIT_FP16X3,
                "l2": "inputs larger than L2 (vertex arrays of up to 171 GB per solve)"}
     else:
         p = CONFIGS[a.workload]
@@ -363,14 +393,18 @@ def main():
             v1, sample1, secs = oracle_sample(small)
             scale = sum(q.n**3 * q.n_Q for q in draw) / (small.n**3 * small.n_Q)
             v = v1 / scale
-            sample = f"{sample1}; smallest solve of the draw (L={small.L}, Nnu={small.n_nu}), x{scale:.0f} by BSE flops"
+            base = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                    "sample": f"{sample1}; smallest solve of the draw (L={small.L}, Nnu={small.n_nu}), "
+                              f"x{scale:.0f} by BSE flops"}
         else:
-            v, sample, secs = oracle_sample(p)
-        cores = blas_threads()
+            base, secs = oracle_baseline(a.workload, target_s=20.0)
+            v = base["value"]
+        # one bounded sample of one iteration, measured once and extrapolated (see cpu_baseline.sample)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-                "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                "steps": 1, "steps_requested": a.steps, "warmup": 0, "extrapolated": True,
+                "ms_per_step": 1e3 / v, "measured_seconds": secs, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "cpu_baseline": base,
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -406,12 +440,12 @@ def main():
                 "peak_source": f"{src} bf16 burst"}
         line = {"metric": METRIC, "value": job_rate(a.steps, world, ms / 1e3), "unit": "batch iter/s (64 solves)",
                 "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[SPLIT_BF16X3],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[cfg["precision"]],
                 "data": "synthetic", "config": dict(cfg, waves=r["waves"]), "roofline": roof,
                 "one_at_a_time": {"value": a.steps / (r["seq_ms"] / 1e3), "unit": "batch iter/s (64 solves)",
                                   "batched_over_one_at_a_time": r["seq_ms"] / r["batch_ms"]},
                 "tuned": r["tuned"], "bse_tflops": bse_tflops, "clocks": r["clocks"],
-                "gpu_launches": ((LAUNCHES_PER_ITER - 1) * 64 + 2) * a.steps,
+                "gpu_launches": ((LAUNCHES_PER_ITER - 1 + (cfg["precision"] == SPLIT_FP16X3)) * 64 + 2) * a.steps,
                 "note": "per memory wave: solves iterated one at a time, then as one batch; times summed"}
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -450,7 +484,9 @@ def main():
         torch.cuda.synchronize()
         fp64_s = time.perf_counter() - t0
         fp64_bse_ms = ref.step_times()["bse"]
-        ref_sig, ref_F, ref_chi = ref.sigma(), ref.F(1, p.n_Q // 2), ref.chi(1)
+        ref_sig = ref.sigma()
+        ref_F = [ref.F(r, p.n_Q // 2) for r in range(4)]
+        ref_chi = [ref.chi(r) for r in range(4)]
         ref.close()
         del ref
         torch.cuda.empty_cache()
@@ -461,8 +497,13 @@ def main():
         return float(np.abs(x - y).max() / np.abs(y).max())
 
     def errors_vs_fp64(sol):
+        # each channel relative to its own max (F at Q = N_Q/2, chi over all Q)
+        eF = [relerr(sol.F(r, p.n_Q // 2), ref_F[r]) for r in range(4)]
+        eC = [relerr(sol.chi(r), ref_chi[r]) for r in range(4)]
         return {"iterations": 2, "sigma_rel_err": relerr(sol.sigma(), ref_sig),
-                "F_m_rel_err": relerr(sol.F(1, p.n_Q // 2), ref_F), "chi_m_rel_err": relerr(sol.chi(1), ref_chi)}
+                "F_rel_err": dict(zip("dmst", eF)), "F_max_rel_err": max(eF),
+                "chi_rel_err": dict(zip("dmst", eC)), "chi_max_rel_err": max(eC),
+                "F_m_rel_err": eF[1], "chi_m_rel_err": eC[1]}
 
     lib_peaks = {"dgemm_tflops": library_gemm_tflops(torch, "fp64"),
                  "tf32_gemm_tflops": library_gemm_tflops(torch, "tf32"),
@@ -473,8 +514,8 @@ def main():
     if compare is not None and not compare.get("extrapolated"):
         solver.iterate(2)
         compare.update(errors_vs_fp64(solver))
-        compare["note"] = ("max-norm errors relative to max|FP64| after two iterations from the zero state; "
-                           "F_m at Q = N_Q/2")
+        compare["note"] = ("max-norm errors relative to max|FP64| of each quantity and channel after two "
+                           "iterations from the zero state; F at Q = N_Q/2, chi over all Q")
     for _ in range(a.warmup):
         solver.iterate(1)
     stream = torch.cuda.current_stream()
@@ -511,7 +552,10 @@ def main():
     full_tr = FULL_TRAFFIC.get((a.workload, a.precision), {}) if a.q_chunk == 0 else {}
     # remap: read 4 Phi, write the BSE operands of 4 channels; BF16 planes are 8 bytes per
     # complex for Gamma X and 12 for F (three pieces), otherwise one complex of esz each
-    remap_bytes = 4.0 * nQ * n * n * (esz + (20 if a.precision == SPLIT_BF16X3 else 2 * esz))
+    # (FP16 planes: 8 + 8 bytes, the twelve complex64 words per (Q, k, k') over the channels;
+    # BF16 planes: 8 + 12 with the third F piece)
+    op_bytes = {SPLIT_BF16X3: 20, SPLIT_FP16X3: 16}.get(a.precision, 2 * esz)
+    remap_bytes = 4.0 * nQ * n * n * (esz + op_bytes)
     bse_tflops = bse_flops / (steps["bse"] * 1e-3) / 1e12
     remap_gbs = remap_bytes / (steps["assemble"] * 1e-3) / 1e9
     if a.precision == FP64:
@@ -523,8 +567,8 @@ def main():
         if a.precision == SPLIT_TF32X3:
             ratio, peak, psrc = None, lib_peaks["tf32_gemm_tflops"], "cuBLAS TF32 GEMM measured live"
         else:
-            ratio = 1.0
-            peak, psrc = pk["bf16_tflops"] * ratio, f"{src} bf16 burst"
+            ratio = 1.0  # FP16 and BF16 inputs run at the same dense tensor rate
+            peak, psrc = pk["bf16_tflops"] * ratio, f"{src} bf16 burst (fp16 dense rate is the same)"
         # DRAM bytes per launch as a multiple of the algorithmic 32 n^2 bytes per GEMM (read A,
         # B, Phi; write Phi)
         tr, tsrc = full_tr.get("bse"), "ncu capture of this launch at full size"
@@ -534,6 +578,7 @@ def main():
                     "frac": bse_tflops / peak, "traffic": tr * 32.0 * n * n * 4 * nQ if tr else None,
                     "traffic_source": tsrc if tr else None,
                     "executed_tensor_frac": 3.0 * bse_tflops / peak,
+                    "executed_note": "the split schemes issue three real products per complex product term",
                     "peak_source": psrc}
     tr = full_tr.get("assemble")
     remap_roof = {"bound": "hbm", "achieved": remap_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -549,40 +594,44 @@ def main():
             "data": "synthetic", "config": cfg, "roofline": roof,
             "kernels": {"ms_per_iter": steps, "bse": bse_roof, "assemble": remap_roof},
             "bse_tflops": bse_tflops, "measured_library_peaks": lib_peaks,
-            "gpu_launches": LAUNCHES_PER_ITER * a.steps, "clocks": clocks,
+            "gpu_launches": (LAUNCHES_PER_ITER + (a.precision == SPLIT_FP16X3)) * a.steps, "clocks": clocks,
             "device_bytes": dev_bytes}
     if compare is not None:
         compare["split_over_fp64"] = value / compare["fp64_iter_per_s"]
         line["fp64_compare"] = compare
-        if a.precision in (SPLIT_TF32X3, SPLIT_BF16X3) and not compare.get("extrapolated"):
-            # the other split scheme on the same workload, for the same comparison
-            alt_prec = SPLIT_TF32X3 if a.precision == SPLIT_BF16X3 else SPLIT_BF16X3
-            other = Solver(p, precision=alt_prec, time_steps=True)
-            other.iterate(2)
-            alt = errors_vs_fp64(other)
-            for _ in range(a.warmup):
-                other.iterate(1)
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            bse_ms = 0.0
-            f0.record(stream)
-            for _ in range(a.steps):
-                other.iterate(1)
-                bse_ms += other.step_times()["bse"]
-            f1.record(stream)
-            torch.cuda.synchronize()
-            alt_ms = f0.elapsed_time(f1)
-            other.close()
-            del other
-            torch.cuda.empty_cache()
-            alt.update({"iter_per_s": a.steps / (alt_ms / 1e3),
-                        "bse_tflops": bse_flops / (bse_ms / a.steps * 1e-3) / 1e12,
-                        "over_fp64": (a.steps / (alt_ms / 1e3)) / compare["fp64_iter_per_s"]})
-            alt_peak = lib_peaks["tf32_gemm_tflops"] if alt_prec == SPLIT_TF32X3 else pk["bf16_tflops"]
-            alt["bse_frac"] = alt["bse_tflops"] / alt_peak
-            alt["executed_tensor_frac"] = 3.0 * alt["bse_tflops"] / alt_peak
-            alt["peak_source"] = "cuBLAS TF32 GEMM measured live" if alt_prec == SPLIT_TF32X3 else f"{src} bf16 burst"
-            line[alt_prec] = alt
+        if a.precision != FP64 and not compare.get("extrapolated"):
+            # the other split schemes on the same workload, for the same comparison
+            for alt_prec in [q for q in (SPLIT_FP16X3, SPLIT_BF16X3, SPLIT_TF32X3) if q != a.precision]:
+                other = Solver(p, precision=alt_prec, time_steps=True)
+                other.iterate(2)
+                alt = errors_vs_fp64(other)
+                for _ in range(a.warmup):
+                    other.iterate(1)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                bse_ms = asm_ms = 0.0
+                f0.record(stream)
+                for _ in range(a.steps):
+                    other.iterate(1)
+                    st_ = other.step_times()
+                    bse_ms += st_["bse"]
+                    asm_ms += st_["assemble"]
+                f1.record(stream)
+                torch.cuda.synchronize()
+                alt_ms = f0.elapsed_time(f1)
+                other.close()
+                del other
+                torch.cuda.empty_cache()
+                alt.update({"iter_per_s": a.steps / (alt_ms / 1e3),
+                            "bse_tflops": bse_flops / (bse_ms / a.steps * 1e-3) / 1e12,
+                            "ms_per_iter": {"bse": bse_ms / a.steps, "assemble": asm_ms / a.steps},
+                            "over_fp64": (a.steps / (alt_ms / 1e3)) / compare["fp64_iter_per_s"]})
+                alt_peak = lib_peaks["tf32_gemm_tflops"] if alt_prec == SPLIT_TF32X3 else pk["bf16_tflops"]
+                alt["bse_frac"] = alt["bse_tflops"] / alt_peak
+                alt["executed_tensor_frac"] = 3.0 * alt["bse_tflops"] / alt_peak
+                alt["peak_source"] = ("cuBLAS TF32 GEMM measured live" if alt_prec == SPLIT_TF32X3
+                                      else f"{src} bf16 burst (fp16 dense rate is the same)")
+                line[alt_prec] = alt
 
     if not a.no_e2e:
         # end to end through the public API: a fresh context (set-up, table uploads), K iterations
@@ -606,9 +655,7 @@ def main():
                        "note": "includes context set-up and the upload of the imaginary-time transform tables"}
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, sample, secs = oracle_sample(p)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"], _ = oracle_baseline(a.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -53,7 +53,8 @@ typedef enum {
   PQ_ENOTCONV = 4, /* pq_iterate reached max_iter above tol (state is valid) */
   PQ_ETIMEOUT = 5, /* a bounded device wait gave up; the context is poisoned */
   PQ_ENAN = 6,     /* a non-finite Sigma appeared; the context is poisoned */
-  PQ_ESTATE = 7    /* the context is poisoned by an earlier PQ_ECUDA/PQ_ENAN */
+  PQ_ESTATE = 7,   /* the context is poisoned by an earlier PQ_ECUDA/PQ_ENAN/PQ_ETIMEOUT */
+  PQ_EDIVERGED = 8 /* pq_iterate stopped: max |dSigma| grew diverge_window times in a row (state is valid) */
 } pq_status;
 
 typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
@@ -67,13 +68,20 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
  *     (~2^-22 per product);
  *   PQ_SPLIT_BF16X3: the assembly writes the operands as BF16 planes (hi/lo;
  *     F also keeps a third piece), the GEMM reads them by TMA with no
- *     conversion (~2^-16 per product, the fastest form);
+ *     conversion (~2^-16 per product);
+ *   PQ_SPLIT_FP16X3: the same with FP16 planes of each channel's operands
+ *     scaled by a power of two (chosen every iteration from bounds of the
+ *     vertex and the bubbles, so every piece lies in the FP16 range): 11-bit
+ *     pieces, ~2^-22 per product at the cost of BF16x3, and the products are
+ *     accumulated in chunks of 256 k that are summed in FP32 registers, so the
+ *     accumulation error does not grow with n;
  *   PQ_SPLIT_BF16X6 is rejected by pq_init with PQ_EINVAL. */
 typedef enum {
   PQ_FP64 = 0,
   PQ_SPLIT_TF32X3 = 1,
   PQ_SPLIT_BF16X3 = 2,
-  PQ_SPLIT_BF16X6 = 3
+  PQ_SPLIT_BF16X6 = 3,
+  PQ_SPLIT_FP16X3 = 4
 } pq_precision;
 
 typedef struct {
@@ -109,6 +117,14 @@ typedef struct {
    * Sigma~1 + Sigma~2 + the box sum of F - F~); 1 Eq. PA_Sigma summed on the vertex box
    * with the vertex cut off at its boundary (zero outside the box), for comparison. */
   int sde;
+  /* Complex output columns per tile of the tensor-core products of the plane formats: 0
+   * (default) 64 for FP16x3 (chunked accumulation) and 128 for BF16x3; 64 or 128 to choose.
+   * FP16x3 accumulates in chunks only with 64-column tiles. */
+  int bse_tile_cols;
+  /* Divergence detection in pq_iterate: when max |dSigma| has grown in each of the last
+   * diverge_window iterations, stop with PQ_EDIVERGED (the iteration that diverges is kept:
+   * the state is valid, e.g. for a restart with stronger mixing).  0 (default): off. */
+  int diverge_window;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */
@@ -144,8 +160,9 @@ PQ_API pq_status pq_set_Lambda(pq_ctx *ctx, int channel, const double *host_c128
 /* Run up to max_iter iterations; stop after the first one whose
  * max_k |Sigma_new(k) - Sigma(k)| < tol.  Writes the count done and the last
  * max |dSigma| when the pointers are non-NULL.  PQ_ENOTCONV if tol was not
- * reached (the state is still valid).  One device->host read of one scalar
- * per iteration. */
+ * reached (the state is still valid); PQ_EDIVERGED if divergence detection
+ * (pq_options.diverge_window) stopped it.  One device->host read of a few
+ * scalars per iteration. */
 PQ_API pq_status pq_iterate(pq_ctx *ctx, int max_iter, double tol, int *iters_done,
                      double *last_max_dsigma);
 
@@ -221,8 +238,9 @@ PQ_API pq_status pq_sigma_second_order_noalloc(int lattice, double beta, double 
  * kernel-function, self-energy and assembly steps, then ONE persistent grouped
  * kernel over the tiles of all members' Bethe-Salpeter products, then a gather
  * of every member's convergence scalars for a single device->host read.
- * Members: contexts made by pq_init with PQ_SPLIT_BF16X3 and a single pass
- * (q_chunk 0 or >= L*L, and the box fits), on one device and one cuda_stream,
+ * Members: contexts made by pq_init with PQ_SPLIT_BF16X3, or all with
+ * PQ_SPLIT_FP16X3, and a single pass (q_chunk 0 or >= L*L, and the box fits),
+ * on one device and one cuda_stream,
  * none poisoned.  The batch does not own them; they must outlive it, and
  * pq_iterate on a member is refused while it exists (the other calls work
  * between batch iterations).  The paper solves one problem at a time; this is
@@ -272,6 +290,15 @@ PQ_API const char *pq_batch_last_error(const pq_batch *b);
 
 /* Release the batch (the members stay valid and can be iterated alone).  NULL is a no-op. */
 PQ_API void pq_batch_destroy(pq_batch *b);
+
+/* Self-test of the bounded device waits, with no fault: one block waits on an
+ * mbarrier that nothing arrives at, for at most limit_ms (1..10000) ms of
+ * global time, then sets the context's wait-timeout flag, exactly as the
+ * tensor-core and gather pipelines do when one of their waits gives up.  The
+ * host side then handles the flag as after an iteration: the call returns
+ * PQ_ETIMEOUT and the context is poisoned (later calls: PQ_ESTATE).  For the
+ * tests of failure handling; the paper has no counterpart. */
+PQ_API pq_status pq_selftest_wait_timeout(pq_ctx *ctx, int limit_ms);
 
 /* Message of the last failure on ctx (or, when ctx is NULL, of the last
  * failed call that has no context: pq_init or pq_sigma_second_order_noalloc). */

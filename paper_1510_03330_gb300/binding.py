@@ -13,15 +13,15 @@ import os
 
 import numpy as np
 
-from .workloads import BETHE, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_TF32X3, Params
+from .workloads import BETHE, FP64, SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_FP16X3, SPLIT_TF32X3, Params
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libparquet_gb300.so")
 
-PQ_OK, PQ_EINVAL, PQ_ENOMEM, PQ_ECUDA, PQ_ENOTCONV, PQ_ETIMEOUT, PQ_ENAN, PQ_ESTATE = range(8)
+PQ_OK, PQ_EINVAL, PQ_ENOMEM, PQ_ECUDA, PQ_ENOTCONV, PQ_ETIMEOUT, PQ_ENAN, PQ_ESTATE, PQ_EDIVERGED = range(9)
 STATUS = {0: "PQ_OK", 1: "PQ_EINVAL", 2: "PQ_ENOMEM", 3: "PQ_ECUDA", 4: "PQ_ENOTCONV", 5: "PQ_ETIMEOUT",
-          6: "PQ_ENAN", 7: "PQ_ESTATE"}
-PRECISION = {FP64: 0, SPLIT_TF32X3: 1, SPLIT_BF16X3: 2, SPLIT_BF16X6: 3}
+          6: "PQ_ENAN", 7: "PQ_ESTATE", 8: "PQ_EDIVERGED"}
+PRECISION = {FP64: 0, SPLIT_TF32X3: 1, SPLIT_BF16X3: 2, SPLIT_BF16X6: 3, SPLIT_FP16X3: 4}
 PQ_NSTEPS = 9
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -43,6 +43,8 @@ class Options(C.Structure):
         ("kernel_level", C.c_int),
         ("edge_rule", C.c_int),
         ("sde", C.c_int),
+        ("bse_tile_cols", C.c_int),
+        ("diverge_window", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -95,6 +97,8 @@ def load_library(path: str = LIB_PATH):
     lib.pq_sigma_second_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
     lib.pq_sigma_second_order_noalloc.restype = C.c_int
+    lib.pq_selftest_wait_timeout.argtypes = [P, C.c_int]
+    lib.pq_selftest_wait_timeout.restype = C.c_int
     lib.pq_set_state.argtypes = [P, D, D]
     lib.pq_set_state.restype = C.c_int
     lib.pq_get_sizes.argtypes = [P, C.POINTER(C.c_longlong)]
@@ -162,7 +166,7 @@ class Solver:
     """One parquet solve on the GPU (C ABI: pq_init ... pq_destroy)."""
 
     def __init__(self, p: Params, precision: str = FP64, time_steps: bool = False, use_torch: bool = True,
-                 q_chunk: int = 0, assembly: int = 0):
+                 q_chunk: int = 0, assembly: int = 0, bse_tile_cols: int = 0, diverge_window: int = 0):
         lib = load_library()
         self.p = p
         self.lib = lib
@@ -180,6 +184,9 @@ class Solver:
         o.kernel_level = p.kernel_level
         o.edge_rule = {"both": 0, "lower": 1}[p.edge_rule]
         o.sde = {"regulated": 0, "truncated": 1}[p.sde]
+        o.bse_tile_cols = bse_tile_cols
+        o.diverge_window = diverge_window
+        self.last_status = PQ_OK
         self._alloc = None
         if use_torch:
             import torch
@@ -227,11 +234,20 @@ class Solver:
 
     # ------------------------------------------------------------------ API
     def iterate(self, max_iter: int = 1, tol: float = 0.0):
-        """Run pq_iterate; returns (iterations done, last max|dSigma|, converged)."""
+        """Run pq_iterate; returns (iterations done, last max|dSigma|, converged).  A run that
+        stops without converging (PQ_ENOTCONV, or PQ_EDIVERGED with divergence detection on)
+        leaves a valid state; its status is kept in last_status."""
         it = C.c_int(0)
         d = C.c_double(0.0)
-        st = self._check(self.lib.pq_iterate(self.h, max_iter, tol, C.byref(it), C.byref(d)), (PQ_OK, PQ_ENOTCONV))
+        st = self._check(self.lib.pq_iterate(self.h, max_iter, tol, C.byref(it), C.byref(d)),
+                         (PQ_OK, PQ_ENOTCONV, PQ_EDIVERGED))
+        self.last_status = st
         return it.value, d.value, st == PQ_OK
+
+    def selftest_wait_timeout(self, limit_ms: int) -> int:
+        """pq_selftest_wait_timeout: a device wait on a barrier nothing arrives at gives up after
+        limit_ms; returns the status (PQ_ETIMEOUT, after which the context is poisoned)."""
+        return self.lib.pq_selftest_wait_timeout(self.h, limit_ms)
 
     def sigma(self) -> np.ndarray:
         p = self.p

@@ -11,7 +11,9 @@
 #include <string>
 #include <vector>
 
+#include "pq_assemble.cuh"
 #include "pq_ctx.h"
+#include "pq_tc.cuh"
 
 using pq::Buffers;
 using pq::Grid;
@@ -112,7 +114,7 @@ size_t vbytes(const pq_ctx *c) {
 
 // Bytes per complex element of the BSE operands (gam, fv) in each storage format.
 size_t gam_es(int vfmt) { return vfmt == pq::V_C128 ? 16 : 8; }
-size_t fv_es(int vfmt) { return vfmt == pq::V_C128 ? 16 : vfmt == pq::V_C64 ? 8 : 12; }
+size_t fv_es(int vfmt) { return vfmt == pq::V_C128 ? 16 : vfmt == pq::V_BF16P ? 12 : 8; }
 
 int num_passes(const pq_ctx *c) { return (c->g.nk + c->b.q_chunk - 1) / c->b.q_chunk; }
 
@@ -142,8 +144,9 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
   CK(pq::launch_tail_and_green(st, g, b));
   mark(1);
   CK(pq::launch_bubbles(st, g, b));
+  if (b.vfmt == pq::V_F16P) CK(pq::launch_split_scales(st, b, c->lam_max));
   mark(2);
-  CK(pq::launch_kernels_extract(st, g, b, c->c64, b.vfmt == pq::V_BF16P && c->krow_ok));
+  CK(pq::launch_kernels_extract(st, g, b, c->c64, pq::split_planes(b.vfmt) && c->krow_ok));
   mark(3);
   if (b.truncated) {
     mark(4);
@@ -177,13 +180,15 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
       cudaEventRecord(c->pev[3 * ip + 1], st);
     }
     void *phi_out = fused ? b.phi : b.phi_new;
-    if (b.vfmt == pq::V_BF16P && ip == 0)  // the products of this iteration sum the new Phi's row edges
+    if (pq::split_planes(b.vfmt) && ip == 0)  // the products of this iteration sum the new Phi's row edges
       CK(cudaMemsetAsync(b.krow, 0, sizeof(double2) * 4 * (size_t)g.n * g.nQ, st));
     if (!bse) {
       // left to the caller
-    } else if (b.vfmt == pq::V_BF16P) {
+    } else if (pq::split_planes(b.vfmt)) {
       const pq::BseProblem *pr = c->probs + (fused ? 0 : (c->swapped ? np : 0) + ip);
-      CK(pq::launch_bse_tma(st, 128, pr, 1, pq::bse_tiles(128, g.n, 4 * zc), (int *)(b.scal + 4), 0));
+      const int bnc = c->bse_cols;
+      CK(pq::launch_bse_tma(st, bnc, b.vfmt == pq::V_F16P, pr, 1, pq::bse_tiles(bnc, g.n, 4 * zc),
+                            (int *)(b.scal + 4), 0));
     } else {
       // in-place products: a separate Jacobi target first receives the old slices
       const size_t es = b.vfmt == pq::V_C128 ? sizeof(double2) : sizeof(float2);
@@ -217,7 +222,7 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
     c->chi_ready = true;
   }
   mark(8);
-  if (b.vfmt == pq::V_BF16P) c->krow_ok = true;
+  if (pq::split_planes(b.vfmt)) c->krow_ok = true;
   return PQ_OK;
 }
 
@@ -274,6 +279,16 @@ pq_status run_iteration(pq_ctx *c, double *dmax) {
 
 }  // namespace
 
+namespace {
+// One thread waits on an mbarrier that expects one arrival which never comes.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int *flag) {
+  __shared__ __align__(8) uint64_t bar;
+  pq::tc::mbar_init(&bar, 1);
+  pq::tc::mbar_fence_init();
+  if (!pq::tc::mbar_wait_ns(&bar, 0, limit_ns)) atomicExch(flag, 1);
+}
+}  // namespace
+
 namespace pq {
 // Message for pq_last_error(NULL) from a call that has no context.
 void set_context_free_error(const char *msg) { g_init_err = msg; }
@@ -308,12 +323,15 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   if (o.sigma2_box_factor < 1) return fail(nullptr, PQ_EINVAL, "sigma2_box_factor must be >= 1");
   if (o.tau_panels < 1 || o.tau_order < 2 || o.tau_matsubara < 1)
     return fail(nullptr, PQ_EINVAL, "bad imaginary-time quadrature sizes");
-  if (o.precision < PQ_FP64 || o.precision > PQ_SPLIT_BF16X6) return fail(nullptr, PQ_EINVAL, "unknown precision");
+  if (o.precision < PQ_FP64 || o.precision > PQ_SPLIT_FP16X3) return fail(nullptr, PQ_EINVAL, "unknown precision");
   if (o.precision == PQ_SPLIT_BF16X6)
     return fail(nullptr, PQ_EINVAL, "BF16x6 split products are not available in this build");
   if (!(o.mix_alpha > 0.0 && o.mix_alpha <= 1.0)) return fail(nullptr, PQ_EINVAL, "mix_alpha must be in (0, 1]");
   if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
     return fail(nullptr, PQ_EINVAL, "dev_alloc and dev_free must be given together");
+  if (o.bse_tile_cols != 0 && o.bse_tile_cols != 64 && o.bse_tile_cols != 128)
+    return fail(nullptr, PQ_EINVAL, "bse_tile_cols must be 0, 64 or 128");
+  if (o.diverge_window < 0) return fail(nullptr, PQ_EINVAL, "diverge_window must be >= 0");
 
   pq_ctx *c = new pq_ctx();
   c->opt = o;
@@ -361,10 +379,16 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   c->lam[2] = -U;
   c->lam[4] = 2.0 * U;
   c->lam[6] = 0.0;
+  for (int r = 0; r < 4; ++r) c->lam_max[r] = std::fabs(c->lam[2 * r]);
 
   Buffers &b = c->b;
-  b.vfmt = o.precision == PQ_FP64 ? pq::V_C128 : o.precision == PQ_SPLIT_TF32X3 ? pq::V_C64 : pq::V_BF16P;
-  b.ld = b.vfmt == pq::V_BF16P ? (g.n + 7) / 8 * 8 : g.n;  // TMA rows: multiples of 16 bytes
+  b.vfmt = o.precision == PQ_FP64            ? pq::V_C128
+           : o.precision == PQ_SPLIT_TF32X3  ? pq::V_C64
+           : o.precision == PQ_SPLIT_FP16X3  ? pq::V_F16P
+                                             : pq::V_BF16P;
+  b.ld = pq::split_planes(b.vfmt) ? (g.n + 7) / 8 * 8 : g.n;  // TMA rows: multiples of 16 bytes
+  // BSE tile: 64 complex columns for FP16 planes (chunked accumulation), else 128
+  c->bse_cols = o.bse_tile_cols ? o.bse_tile_cols : (b.vfmt == pq::V_F16P ? 64 : 128);
   if (o.q_chunk < 0) {
     delete c;
     return fail(nullptr, PQ_EINVAL, "q_chunk must be >= 0");
@@ -438,7 +462,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       {(void **)&b.k1, cs * 4 * g.nQ},
       {(void **)&b.k2row, cs * 4 * (size_t)g.n * g.nQ},
       {(void **)&b.k2col, cs * 4 * (size_t)g.n * g.nQ},
-      {(void **)&b.krow, b.vfmt == pq::V_BF16P ? cs * 4 * (size_t)g.n * g.nQ : 0},
+      {(void **)&b.krow, pq::split_planes(b.vfmt) ? cs * 4 * (size_t)g.n * g.nQ : 0},
+      {(void **)&b.fsc, b.vfmt == pq::V_F16P ? sizeof(float) * pq::FSC_N : 0},
       {(void **)&b.dfpart, cs * (size_t)g.n * g.nk},
       {(void **)&b.scal, 8 * sizeof(double)},
       {(void **)&b.s1_R, cs * g.nk * 2 * (size_t)z.M},
@@ -514,7 +539,9 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     cudaError_t e1 = cudaMemset(b.phi, 0, vb);
     cudaError_t e2 = cudaMemset(b.sigma, 0, cs * g.nk * g.n_ext);
     cudaError_t e3 = cudaMemset(b.scal, 0, 8 * sizeof(double));
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) s = fail(c, PQ_ECUDA, "memset failed");
+    cudaError_t e4 = b.fsc ? cudaMemset(b.fsc, 0, sizeof(float) * pq::FSC_N) : cudaSuccess;
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess)
+      s = fail(c, PQ_ECUDA, "memset failed");
   }
   for (int i = 0; s == PQ_OK && i <= PQ_NSTEPS; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) s = fail(c, PQ_ECUDA, "event create failed");
@@ -523,10 +550,10 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     for (auto &e : c->pev)
       if (s == PQ_OK && cudaEventCreate(&e) != cudaSuccess) s = fail(c, PQ_ECUDA, "event create failed");
   }
-  if (s == PQ_OK && b.vfmt == pq::V_BF16P) {
+  if (s == PQ_OK && pq::split_planes(b.vfmt)) {
     // problem table of the TMA-fed BSE: per pass, and per assignment of the Phi buffers
     CUtensorMap mA, mB;
-    CUresult r = pq::make_bse_maps(b.gam, b.fv, g.n, b.ld, 4LL * b.q_chunk * g.n_om, &mA, &mB);
+    CUresult r = pq::make_bse_maps(b.gam, b.fv, g.n, b.ld, 4LL * b.q_chunk * g.n_om, b.vfmt == pq::V_F16P, &mA, &mB);
     if (r != CUDA_SUCCESS) s = fail(c, PQ_ECUDA, "tensor map encoding failed (CUresult %d)", (int)r);
     const int np = num_passes(c);
     std::vector<pq::BseProblem> tab(several ? 2 * np : 1);
@@ -549,6 +576,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       e.alpha = (float)g.mix;
       e.n_nu = g.n_nu;
       e.krow = b.krow;
+      e.uns = b.vfmt == pq::V_F16P ? b.fsc + pq::FSC_UNS : nullptr;
+      e.phimax = b.vfmt == pq::V_F16P ? (unsigned *)(b.fsc + pq::FSC_PHIMAX) : nullptr;
     }
     c->prob_host = tab[0];
     if (s == PQ_OK) {
@@ -586,6 +615,10 @@ pq_status pq_set_Lambda(pq_ctx *c, int channel, const double *host_c128, int n_l
   }
   c->b.lam_tab[channel] = d;  // a previous table stays allocated until pq_destroy
   c->b.lam_nl[channel] = n_lambda;
+  // bound of |Re|, |Im| of this channel's Lambda (table and constant), for the FP16 scales
+  double lm = std::fabs(c->lam[2 * channel]);
+  for (size_t i = 0; i < 2 * cnt; ++i) lm = std::max(lm, std::fabs(host_c128[i]));
+  c->lam_max[channel] = lm;
   return PQ_OK;
 }
 
@@ -594,8 +627,9 @@ pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, doubl
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned by an earlier error: %s", c->err.c_str());
   if (max_iter < 0) return fail(c, PQ_EINVAL, "max_iter < 0");
   if (c->in_batch) return fail(c, PQ_EINVAL, "the context belongs to a batch: iterate it with pq_batch_iterate");
-  double d = INFINITY;
-  int it = 0;
+  double d = INFINITY, prev = INFINITY;
+  int it = 0, grown = 0;
+  const int win = c->opt.diverge_window;
   for (; it < max_iter; ++it) {
     pq_status s = run_iteration(c, &d);
     if (s != PQ_OK) {
@@ -605,6 +639,13 @@ pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, doubl
     if (d < tol) {
       ++it;
       break;
+    }
+    grown = d > prev ? grown + 1 : 0;  // consecutive iterations whose max |dSigma| grew
+    prev = d;
+    if (win > 0 && grown >= win) {
+      if (iters_done) *iters_done = it + 1;
+      if (last) *last = d;
+      return fail(c, PQ_EDIVERGED, "max |dSigma| grew in each of the last %d iterations (now %.3e)", win, d);
     }
   }
   if (iters_done) *iters_done = it;
@@ -670,6 +711,21 @@ pq_status pq_get_F(const pq_ctx *cc, int channel, int Q, double *out, size_t len
       out[2 * i] = tmp[i].x;
       out[2 * i + 1] = tmp[i].y;
     }
+  } else if (b.vfmt == pq::V_F16P) {
+    // four FP16 planes (Re h, Im h, Re l, Im l) of the scaled value: (h + l) / scale
+    const size_t ps = (size_t)4 * b.q_chunk * g.n_om * n * ld;
+    std::vector<uint16_t> tmp(4 * n * ld);
+    for (int w = 0; w < 4; ++w)
+      CK(cudaMemcpy(tmp.data() + w * n * ld, (const uint16_t *)b.fv + w * ps + slab * n * ld, n * ld * 2,
+                    cudaMemcpyDeviceToHost));
+    float sb = 1.f;
+    CK(cudaMemcpy(&sb, b.fsc + pq::FSC_SB + channel, sizeof sb, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i)
+      for (size_t j = 0; j < n; ++j) {
+        const size_t e = i * ld + j;
+        out[2 * (i * n + j)] = ((double)pq::f16_value(tmp[e]) + pq::f16_value(tmp[2 * n * ld + e])) / sb;
+        out[2 * (i * n + j) + 1] = ((double)pq::f16_value(tmp[n * ld + e]) + pq::f16_value(tmp[3 * n * ld + e])) / sb;
+      }
   } else {
     // six BF16 planes (Re h, Im h, Re l, Im l, Re r, Im r); element value = h + l + r
     const size_t ps = (size_t)4 * b.q_chunk * g.n_om * n * ld;  // plane stride of the buffer
@@ -746,6 +802,18 @@ pq_status pq_set_state(pq_ctx *c, const double *phi, const double *sigma) {
   if (sigma) CK(cudaMemcpy(c->b.sigma, sigma, sizeof(double2) * c->g.nk * c->g.n_ext, cudaMemcpyHostToDevice));
   if (phi) {
     const long long ne = 4LL * c->g.nQ * c->g.n * c->g.n;
+    if (c->b.fsc) {
+      // largest |Re|, |Im| per channel of the stored (complex64) Phi: the FP16 scales of the
+      // next iteration derive from it
+      float mx[4] = {0.f, 0.f, 0.f, 0.f};
+      const long long per = ne / 4;
+      for (long long i = 0; i < ne; ++i) {
+        const float a = std::fabs((float)phi[2 * i]), b2 = std::fabs((float)phi[2 * i + 1]);
+        float &m = mx[i / per];
+        m = std::max(m, std::max(a, b2));
+      }
+      CK(cudaMemcpy(c->b.fsc + pq::FSC_PHIMAX, mx, sizeof mx, cudaMemcpyHostToDevice));
+    }
     if (!c->c64) {
       CK(cudaMemcpy(c->b.phi, phi, ne * sizeof(double2), cudaMemcpyHostToDevice));
     } else {
@@ -785,6 +853,19 @@ pq_status pq_step_times(const pq_ctx *c, float *out, int n) {
 }
 
 const char *pq_step_name(int i) { return (i >= 0 && i < PQ_NSTEPS) ? kStepNames[i] : ""; }
+
+pq_status pq_selftest_wait_timeout(pq_ctx *c, int limit_ms) {
+  if (!c) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (limit_ms < 1 || limit_ms > 10000) return fail(c, PQ_EINVAL, "limit_ms must be in [1, 10000]");
+  wait_selftest_kernel<<<1, 1, 0, c->st>>>((uint64_t)limit_ms * 1000000ull, (int *)(c->b.scal + 4));
+  CK(cudaGetLastError());
+  double h[5];
+  CK(cudaMemcpyAsync(h, c->b.scal, sizeof h, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double d = 0.0;
+  return pq::finish_iteration(c, h, &d, false);
+}
 
 const char *pq_last_error(const pq_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 

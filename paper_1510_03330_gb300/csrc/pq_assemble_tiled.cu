@@ -1,7 +1,7 @@
-// Tiled parquet assembly for the BF16x3 path: the parquet equations with the kernel fill
-// (Eq. PA_F; App. A, Eqs. PA_Gamma_dm, PA_Gamma_st; Sec. II.A), F = Gamma + Phi, the BSE
-// left operand s_r Gamma_r diag(X_r) (Eq. PA_F_Phi) split into BF16 planes, and the box sum
-// of Eq. PA_Sigma over F - Lambda^0 (Sec. II.B).  The arithmetic per element is that of the
+// Tiled parquet assembly for the split paths that write operand planes (BF16x3, FP16x3): the
+// parquet equations with the kernel fill (Eq. PA_F; App. A, Eqs. PA_Gamma_dm, PA_Gamma_st;
+// Sec. II.A), F = Gamma + Phi, the BSE left operand s_r Gamma_r diag(X_r) (Eq. PA_F_Phi) split
+// into BF16 or FP16 planes, and the box sum of Eq. PA_Sigma over F - Lambda^0 (Sec. II.B).  The arithmetic per element is that of the
 // general assembly in pq_vertex.cu; what differs is how the work is cut, so that every
 // operand row is written in runs of G * Nnu contiguous columns instead of Nnu.
 //
@@ -159,6 +159,45 @@ __device__ inline void put4(uint16_t *gam, uint16_t *fv, long long ps, long long
   *(uint2 *)(fv + 5 * ps + o) = fi.r;
 }
 
+// FP16 planes: the same four k' of Gamma X (scaled by sa) and F (scaled by sb) as h + l, planes
+// Gamma X (Re h, Re l, Im h, Im l) and F (Re h, Im h, Re l, Im l).
+__device__ inline uint2 pack4h(const uint32_t *v) { return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16)); }
+__device__ inline void split4h(float sc, float x0, float x1, float x2, float x3, uint2 &h, uint2 &l) {
+  uint32_t hv[4], lv[4];
+  f16_split(sc * x0, hv[0], lv[0]);
+  f16_split(sc * x1, hv[1], lv[1]);
+  f16_split(sc * x2, hv[2], lv[2]);
+  f16_split(sc * x3, hv[3], lv[3]);
+  h = pack4h(hv);
+  l = pack4h(lv);
+}
+__device__ inline void put4h(uint16_t *gam, uint16_t *fv, long long ps, long long o, const float2 *gx,
+                             const float2 *f, float sa, float sb) {
+  uint2 h, l;
+  split4h(sa, gx[0].x, gx[1].x, gx[2].x, gx[3].x, h, l);
+  *(uint2 *)(gam + o) = h;
+  *(uint2 *)(gam + ps + o) = l;
+  split4h(sa, gx[0].y, gx[1].y, gx[2].y, gx[3].y, h, l);
+  *(uint2 *)(gam + 2 * ps + o) = h;
+  *(uint2 *)(gam + 3 * ps + o) = l;
+  split4h(sb, f[0].x, f[1].x, f[2].x, f[3].x, h, l);
+  *(uint2 *)(fv + o) = h;
+  *(uint2 *)(fv + 2 * ps + o) = l;
+  split4h(sb, f[0].y, f[1].y, f[2].y, f[3].y, h, l);
+  *(uint2 *)(fv + ps + o) = h;
+  *(uint2 *)(fv + 3 * ps + o) = l;
+}
+
+// Operand output of channel r in the plane format PF (V_BF16P or V_F16P).
+template <int PF>
+__device__ inline void put_ops(uint16_t *gam, uint16_t *fv, long long ps, long long o, const float2 *gx,
+                               const float2 *f, const float *ssc, int r) {
+  if constexpr (PF == V_F16P)
+    put4h(gam, fv, ps, o, gx, f, ssc[r], ssc[4 + r]);
+  else
+    put4(gam, fv, ps, o, gx, f);
+}
+
 __device__ inline float2 f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // Everything one thread needs to evaluate its four elements of a step.
@@ -257,15 +296,17 @@ __device__ inline void load4(const float2 *p, float2 *v) {
 
 // FUSED: one gather per q, s/t rows completed through the delay line (needs rows == NOmega).
 // Otherwise: two gathers per target momentum of the pass.
-template <bool FUSED, bool TAB>
+template <bool FUSED, bool TAB, int PF>
 __global__ void __launch_bounds__(TT, 2)
     assemble_tiled_kernel(Grid g, TGeo t, const float2 *__restrict__ phi, uint16_t *__restrict__ gam,
                           uint16_t *__restrict__ fv, long long ps, int ld, const double2 *__restrict__ k1,
                           const double2 *__restrict__ k2row, const float2 *__restrict__ xph,
                           const float2 *__restrict__ xpp, const float2 *__restrict__ gtab,
-                          double2 *__restrict__ dfpart, Lam lam, Pass pass, int *err) {
+                          double2 *__restrict__ dfpart, Lam lam, Pass pass, const float *__restrict__ fsc,
+                          int *err) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double2 red[TT];
+  __shared__ float ssc[8];  // FP16 planes: scales of Gamma X and F per channel
   __shared__ int abort_flag;
   __shared__ int stab[2][4 * T_N];  // step tables of this step and the next
   float2 *Rt = (float2 *)(smem + t.oR), *Pt = (float2 *)(smem + t.oP), *St = (float2 *)(smem + t.oS);
@@ -294,6 +335,7 @@ __global__ void __launch_bounds__(TT, 2)
   auto step_q = [&](int st) { return FUSED ? st : pass.qb + st / 2; };
   auto step_dm = [&](int st) { return FUSED || (st & 1) == 0; };
   if (tid < G) step_table(g, step_dm(0), step_q(0), ik, p0, tid, stab[0] + tid * T_N);
+  if (PF == V_F16P && tid < 8) ssc[tid] = fsc[tid < 4 ? FSC_SA + tid : FSC_SB + tid - 4];
   if (tid == 0) {
     abort_flag = 0;
     tc::mbar_init(bar, 1);
@@ -340,8 +382,8 @@ __global__ void __launch_bounds__(TT, 2)
         const float2 gkq = gtab[(long long)tb[T_CM] * g.n_g + (n + m - g.g_lo)];
         elems_dm<TAB>(g, c, lam, l0, l1, twoU, xq, gkq, gx, f, acc);
         const long long o = ((long long)(Q - pass.qb * nom) * nn + k) * ld + col0;
-        put4(gam, fv, ps, o, gx[0], f[0]);
-        put4(gam, fv, ps, ochan + o, gx[1], f[1]);
+        put_ops<PF>(gam, fv, ps, o, gx[0], f[0], ssc, 0);
+        put_ops<PF>(gam, fv, ps, ochan + o, gx[1], f[1], ssc, 1);
       }
       if (do_st) {
         const int qp = tb[a * T_N + T_QS];  // q' of this thread's block
@@ -375,15 +417,15 @@ __global__ void __launch_bounds__(TT, 2)
             }
             const int q0 = tb[T_Q0];
             const long long o = ((long long)(q0 * nom + mi) * nn + k) * ld + col0;
-            put4(gam, fv, ps, 2 * ochan + o, wg[0], wf[0]);
-            put4(gam, fv, ps, 3 * ochan + o, wg[1], wf[1]);
+            put_ops<PF>(gam, fv, ps, 2 * ochan + o, wg[0], wf[0], ssc, 2);
+            put_ops<PF>(gam, fv, ps, 3 * ochan + o, wg[1], wf[1], ssc, 3);
           }
           if (a > 0) {
             if (qy + a >= g.L) {
               // block 0 of this row came earlier in the lattice row of q: store this block alone
               const long long o = ((long long)Qp * nn + k) * ld + col0;
-              put4(gam, fv, ps, 2 * ochan + o, gx[0], f[0]);
-              put4(gam, fv, ps, 3 * ochan + o, gx[1], f[1]);
+              put_ops<PF>(gam, fv, ps, 2 * ochan + o, gx[0], f[0], ssc, 2);
+              put_ops<PF>(gam, fv, ps, 3 * ochan + o, gx[1], f[1], ssc, 3);
             } else {
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
@@ -396,8 +438,8 @@ __global__ void __launch_bounds__(TT, 2)
           }
         } else {
           const long long o = ((long long)(Qp - pass.qb * nom) * nn + k) * ld + col0;
-          put4(gam, fv, ps, 2 * ochan + o, gx[0], f[0]);
-          put4(gam, fv, ps, 3 * ochan + o, gx[1], f[1]);
+          put_ops<PF>(gam, fv, ps, 2 * ochan + o, gx[0], f[0], ssc, 2);
+          put_ops<PF>(gam, fv, ps, 3 * ochan + o, gx[1], f[1], ssc, 3);
         }
       }
     }
@@ -484,16 +526,24 @@ bool tiled_geo(const Grid &g, bool fused, TGeo &t) {
   return any;
 }
 
-template <bool FUSED, bool TAB>
+template <bool FUSED, bool TAB, int PF>
 cudaError_t tiled_launch(cudaStream_t st, const Grid &g, const TGeo &t, Buffers &b, const Lam &lam, const Pass &p,
                          long long ps) {
-  auto kfn = assemble_tiled_kernel<FUSED, TAB>;
+  auto kfn = assemble_tiled_kernel<FUSED, TAB, PF>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
   if (e != cudaSuccess) return e;
   kfn<<<dim3(g.nk / t.G, g.n), t.nthr, t.smem, st>>>(
       g, t, (const float2 *)b.phi, (uint16_t *)b.gam, (uint16_t *)b.fv, ps, b.ld, b.k1, b.k2row, b.xph32, b.xpp32,
-      b.gtab32, b.dfpart, lam, p, (int *)(b.scal + 4));
+      b.gtab32, b.dfpart, lam, p, b.fsc, (int *)(b.scal + 4));
   return cudaGetLastError();
+}
+
+template <int PF>
+cudaError_t tiled_dispatch(cudaStream_t st, const Grid &g, const TGeo &t, bool fused, bool tab, Buffers &b,
+                           const Lam &lam, const Pass &p, long long ps) {
+  if (fused)
+    return tab ? tiled_launch<true, true, PF>(st, g, t, b, lam, p, ps) : tiled_launch<true, false, PF>(st, g, t, b, lam, p, ps);
+  return tab ? tiled_launch<false, true, PF>(st, g, t, b, lam, p, ps) : tiled_launch<false, false, PF>(st, g, t, b, lam, p, ps);
 }
 
 }  // namespace
@@ -508,8 +558,8 @@ cudaError_t launch_assemble_tiled(cudaStream_t st, const Grid &g, Buffers &b, co
   TGeo t;
   const bool fused = p.fused && tiled_geo(g, true, t);
   if (!fused && !tiled_geo(g, false, t)) return cudaErrorInvalidValue;
-  if (fused) return tab ? tiled_launch<true, true>(st, g, t, b, lam, p, ps) : tiled_launch<true, false>(st, g, t, b, lam, p, ps);
-  return tab ? tiled_launch<false, true>(st, g, t, b, lam, p, ps) : tiled_launch<false, false>(st, g, t, b, lam, p, ps);
+  if (b.vfmt == V_F16P) return tiled_dispatch<V_F16P>(st, g, t, fused, tab, b, lam, p, ps);
+  return tiled_dispatch<V_BF16P>(st, g, t, fused, tab, b, lam, p, ps);
 }
 
 }  // namespace pq

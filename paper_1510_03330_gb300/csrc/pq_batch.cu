@@ -112,7 +112,8 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph
     BCK(cudaStreamWaitEvent(b->st, b->join[j], 0));
   }
   if (timing) BCK(rec(b->ev[1]));
-  BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->tab[ti][order], (int)b->m.size(), b->tiles[ti], b->err, 0));
+  BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->m[0]->b.vfmt == pq::V_F16P, b->tab[ti][order], (int)b->m.size(),
+                         b->tiles[ti], b->err, 0));
   if (timing) BCK(rec(b->ev[2]));
   const int n = (int)b->m.size();
   gather_kernel<<<(n + 127) / 128, 128, 0, b->st>>>(b->scal, n, b->err, b->gather);
@@ -185,7 +186,10 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
       if (ctxs[j] == c) return bfail(nullptr, PQ_EINVAL, "member %d appears twice", i);
     if (c->poisoned) return bfail(nullptr, PQ_EINVAL, "member %d is poisoned", i);
     if (c->in_batch) return bfail(nullptr, PQ_EINVAL, "member %d already belongs to a batch", i);
-    if (c->b.vfmt != pq::V_BF16P) return bfail(nullptr, PQ_EINVAL, "member %d is not PQ_SPLIT_BF16X3", i);
+    if (!pq::split_planes(c->b.vfmt))
+      return bfail(nullptr, PQ_EINVAL, "member %d is neither PQ_SPLIT_BF16X3 nor PQ_SPLIT_FP16X3", i);
+    if (c->b.vfmt != ctxs[0]->b.vfmt)
+      return bfail(nullptr, PQ_EINVAL, "member %d has another operand format than member 0", i);
     if (c->b.q_chunk < c->g.nk) return bfail(nullptr, PQ_EINVAL, "member %d runs in several passes", i);
     if (c->st != ctxs[0]->st) return bfail(nullptr, PQ_EINVAL, "member %d uses another stream", i);
   }

@@ -33,7 +33,9 @@ struct pq_ctx {
   bool chi_ready = false;        // chi computed during the last iteration (several passes)
   pq::BseProblem prob_host{};    // the single-pass entry of the table (for batches)
   bool in_batch = false;         // a batch holds this context: pq_iterate is refused
-  bool krow_ok = false;          // BF16x3: b.krow holds the edge row sums of the current Phi
+  bool krow_ok = false;          // split planes: b.krow holds the edge row sums of the current Phi
+  double lam_max[4] = {0, 0, 0, 0};  // max |Re|, |Im| of Lambda per channel (FP16 scales)
+  int bse_cols = 128;            // complex output columns per tile of the TMA-fed products
 };
 
 

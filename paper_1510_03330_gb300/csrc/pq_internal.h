@@ -53,10 +53,17 @@ struct Buffers {
   // Storage of the BSE operands gam and fv:
   //   V_C128 / V_C64: [r][Q][k][ld] complex of the storage type;
   //   V_BF16P: BF16 planes [plane][r][Q][k][ld]; gam planes (Re h, Re l, Im h, Im l),
-  //   fv planes (Re h, Im h, Re l, Im l, Re r, Im r) with x = h + l + r.
+  //   fv planes (Re h, Im h, Re l, Im l, Re r, Im r) with x = h + l + r;
+  //   V_F16P: FP16 planes of the same order, gam (Re h, Re l, Im h, Im l), fv (Re h, Im h,
+  //   Re l, Im l), with x * 2^e = h + l (no third piece).
   const void *lam_tab[4] = {};  // tabulated local Lambda per channel (arithmetic type of the assembly)
   int lam_nl[4] = {};
-  double2 *krow = nullptr;       // BF16x3: edge row sums of Phi accumulated by the BSE epilogue
+  double2 *krow = nullptr;       // split planes: edge row sums of Phi accumulated by the BSE epilogue
+  // FP16 planes: power-of-two scales of the split operands, [0..3] max |Re|, |Im| of the state's
+  // Phi per channel (float bits, accumulated by the products that write it), [4..5] the same of
+  // X_ph, X_pp (accumulated by the bubbles), [8..11] scale of Gamma X, [12..15] scale of F,
+  // [16..19] 1 / (scale of Gamma X * scale of F), per channel
+  float *fsc = nullptr;
   int vfmt = 0;
   int assembly = 0;              // BF16x3 assembly kernel: 0 tiled where the shape allows, 1 general
   bool first_level = false;      // kernel approximation of the fill: K1 only (else K1 + K2)
@@ -67,7 +74,11 @@ struct Buffers {
   void *phi_new = nullptr;       // Jacobi target when the transfers run in several passes
 };
 
-enum VFmt { V_C128 = 0, V_C64 = 1, V_BF16P = 2 };
+// V_BF16P: BF16 planes, x = h + l (+ r for F); V_F16P: FP16 planes of the scaled value,
+// x * 2^e = h + l, with the power-of-two scale 2^e of the channel in Buffers::fsc.
+enum VFmt { V_C128 = 0, V_C64 = 1, V_BF16P = 2, V_F16P = 3 };
+inline bool split_planes(int vfmt) { return vfmt == V_BF16P || vfmt == V_F16P; }
+enum { FSC_PHIMAX = 0, FSC_XMAX = 4, FSC_SA = 8, FSC_SB = 12, FSC_UNS = 16, FSC_N = 32 };
 
 // One pass of the assembly and the BSE over the transfers Q = (q, m) with
 // q-momentum in [qb, qb + nq): the operand buffers hold 4 * nq * NOmega slices.
@@ -105,6 +116,10 @@ cudaError_t zgemm_fp64(cudaStream_t st, int M, int N, int K, double2 alpha, cons
 // one-particle steps (pq_onebody.cu)
 cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b);
 cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b);
+// FP16 planes: the power-of-two scales of this iteration's operands from the state's vertex
+// bound and the bubbles' bound (lam_max: max |Re|, |Im| of Lambda per channel); resets the
+// bounds that the bubbles and the products accumulate for the next iteration
+cudaError_t launch_split_scales(cudaStream_t st, Buffers &b, const double *lam_max);
 cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const Sigma1Args &a);
 Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *out);
 cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1);
@@ -146,13 +161,17 @@ struct BseProblem {
   float alpha;
   int n_nu;           // fermionic frequencies per momentum block (edge test of the row sums)
   double2 *krow;      // if set: [r][k][Q] += sum of the new Phi row k over the k' frequency edges
+  const float *uns;   // if set (FP16 planes): the product of channel r is multiplied by uns[r]
+  unsigned *phimax;   // if set: [r] = max of the bits of |Re|, |Im| over the new Phi of channel r
 };
 size_t bse_tma_smem_bytes(int bnc);
 long long bse_tiles(int bnc, int n, int batch);
-CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long long slabs, CUtensorMap *mapA,
-                       CUtensorMap *mapB);
-// bnc: complex output columns per tile (128 or 64); max_ctas > 0 caps the persistent grid
-cudaError_t launch_bse_tma(cudaStream_t st, int bnc, const BseProblem *probs, int nprob, long long tiles,
+// f16: FP16 planes (four F planes), else BF16 planes (six F planes)
+CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long long slabs, bool f16,
+                       CUtensorMap *mapA, CUtensorMap *mapB);
+// bnc: complex output columns per tile (128 or 64); f16: FP16 operand planes, else BF16;
+// max_ctas > 0 caps the persistent grid
+cudaError_t launch_bse_tma(cudaStream_t st, int bnc, bool f16, const BseProblem *probs, int nprob, long long tiles,
                            int *err, int max_ctas);
 
 // Sigma~2 (pq_sigma2.cu)

@@ -7,6 +7,7 @@
 
 #include <cuda_bf16.h>
 
+#include "pq_assemble.cuh"
 #include "pq_common.cuh"
 #include "pq_internal.h"
 
@@ -55,10 +56,41 @@ __device__ inline double2 gt(const Grid &g, const double2 *gtab, int ik, int n) 
   return gtab[(long long)ik * g.n_g + (n - g.g_lo)];
 }
 
-// X_ph(Q,k) = (T/N) G(k) G(k+q), X_pp(Q,k) = (T/N) G(k) G(q-k).
+// X_ph(Q,k) = (T/N) G(k) G(k+q), X_pp(Q,k) = (T/N) G(k) G(q-k).  With xmax (FP16 planes), the
+// largest |Re|, |Im| of the FP32 copies of X_ph and X_pp are accumulated into xmax[0], xmax[1]
+// (float bits: for non-negative floats the integer order is the numeric order).
 __global__ void bubbles_kernel(Grid g, const double2 *__restrict__ gtab, double2 *__restrict__ xph,
-                               double2 *__restrict__ xpp, float2 *__restrict__ xph32, float2 *__restrict__ xpp32) {
+                               double2 *__restrict__ xpp, float2 *__restrict__ xph32, float2 *__restrict__ xpp32,
+                               unsigned *__restrict__ xmax) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (xmax) {
+    float mph = 0.f, mpp = 0.f;
+    if (i < (long long)g.nQ * g.n) {
+      const int Q = (int)(i / g.n), k = (int)(i % g.n);
+      const int iq = Q / g.n_om, m = g.m_lo + Q % g.n_om;
+      const int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
+      const double c = g.T / g.nk;
+      const double2 gk = gt(g, gtab, ik, n);
+      const double2 a = c * cmul(gk, gt(g, gtab, kadd(g, ik, iq), n + m));
+      const double2 b = c * cmul(gk, gt(g, gtab, ksub(g, iq, ik), m - n - 1));
+      const float2 a32 = make_float2((float)a.x, (float)a.y), b32 = make_float2((float)b.x, (float)b.y);
+      xph[i] = a;
+      xpp[i] = b;
+      xph32[i] = a32;
+      xpp32[i] = b32;
+      mph = fmaxf(fabsf(a32.x), fabsf(a32.y));
+      mpp = fmaxf(fabsf(b32.x), fabsf(b32.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mph = fmaxf(mph, __shfl_xor_sync(0xffffffffu, mph, o));
+      mpp = fmaxf(mpp, __shfl_xor_sync(0xffffffffu, mpp, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&xmax[0], __float_as_uint(mph));
+      atomicMax(&xmax[1], __float_as_uint(mpp));
+    }
+    return;
+  }
   if (i >= (long long)g.nQ * g.n) return;
   int Q = (int)(i / g.n), k = (int)(i % g.n);
   int iq = Q / g.n_om, m = g.m_lo + Q % g.n_om;
@@ -73,6 +105,51 @@ __global__ void bubbles_kernel(Grid g, const double2 *__restrict__ gtab, double2
     xph32[i] = make_float2((float)a.x, (float)a.y);
     xpp32[i] = make_float2((float)b.x, (float)b.y);
   }
+}
+
+// Power-of-two scales of the FP16 operand planes of one iteration (one thread).  Per channel r,
+// bounds of |Re| and |Im| follow from the state's bounds p_x (max over Phi_x of |Re|, |Im|),
+// the bubbles' bounds and those of Lambda: a parquet-equation lookup is a stored Phi_x or a
+// fill K1 + K2row + K2col = (row mean) + (column mean) - K1, at most 3 p_x, so
+//   |Gamma_r| <= lam_r + 3 sum_i |c_i^r| p_{x_i}   (Eqs. PA_Gamma_dm, PA_Gamma_st),
+//   |F_r| <= |Gamma_r| + p_r,   |s_r Gamma_r X_r| <= |s_r| 2 |Gamma_r| xmax_r.
+// The scale 2^e of each operand maps its bound into [2^14, 2^15), inside the FP16 range.
+// The bounds of the next state and bubbles are then reset: the products and the bubbles of
+// this iteration accumulate them.
+__device__ inline float pow2_scale(float bound) {
+  if (!(bound > 0.f) || !isfinite(bound)) return 1.f;
+  int e;
+  frexpf(bound, &e);  // bound = f 2^e, f in [0.5, 1)
+  e = max(-100, min(100, 15 - e));
+  return ldexpf(1.f, e);
+}
+
+struct Bound4 {
+  float v[4];
+};
+
+__global__ void split_scales_kernel(float *fsc, Bound4 lam_max) {
+  unsigned *u = (unsigned *)fsc;
+  const float p[4] = {__uint_as_float(u[FSC_PHIMAX]), __uint_as_float(u[FSC_PHIMAX + 1]),
+                      __uint_as_float(u[FSC_PHIMAX + 2]), __uint_as_float(u[FSC_PHIMAX + 3])};
+  const float xm[2] = {__uint_as_float(u[FSC_XMAX]), __uint_as_float(u[FSC_XMAX + 1])};
+  const float *lam = lam_max.v;
+  // sum_i |c_i^r| p_{x_i} of the four crossed terms of each channel
+  const float cp[4] = {0.5f * p[0] + 1.5f * p[1] + 0.5f * p[2] + 1.5f * p[3],
+                       0.5f * (p[0] + p[1] + p[2] + p[3]),
+                       p[0] + 3.0f * p[1],
+                       p[0] + p[1]};
+  const float s_abs[4] = {1.f, 1.f, 0.5f, 0.5f};
+  for (int r = 0; r < 4; ++r) {
+    const float gam = lam[r] + 3.0f * cp[r];
+    const float sa = pow2_scale(s_abs[r] * 2.0f * gam * xm[r < 2 ? 0 : 1]);
+    const float sb = pow2_scale(gam + p[r]);
+    fsc[FSC_SA + r] = sa;
+    fsc[FSC_SB + r] = sb;
+    fsc[FSC_UNS + r] = 1.f / (sa * sb);
+    u[FSC_PHIMAX + r] = 0u;
+  }
+  u[FSC_XMAX] = u[FSC_XMAX + 1] = 0u;
 }
 
 // Tail moments of G = 1/(i nu) + c2/(i nu)^2 + c3/(i nu)^3 + O(nu^-4).
@@ -166,9 +243,14 @@ __device__ inline double2 f_elem64(const void *fv, long long e) { return ((const
 // Element e of the F operand buffer of a split path in FP32: the complex64 value, or the sum
 // of the three BF16 pieces (h + l is exact; adding r rounds once, at 2^-24 relative).
 template <int FMT>
-__device__ inline float2 f_elem32(const void *fv, long long ps, long long e) {
+__device__ inline float2 f_elem32(const void *fv, long long ps, long long e, float inv_sb = 1.f) {
   if constexpr (FMT == V_C64) {
     return ((const float2 *)fv)[e];
+  } else if constexpr (FMT == V_F16P) {
+    // FP16 planes (Re h, Im h, Re l, Im l) of the scaled value: (h + l) / scale, exact in FP32
+    const uint16_t *p = (const uint16_t *)fv;
+    return make_float2((f16_value(p[e]) + f16_value(p[2 * ps + e])) * inv_sb,
+                       (f16_value(p[ps + e]) + f16_value(p[3 * ps + e])) * inv_sb);
   } else {
     const uint16_t *p = (const uint16_t *)fv;
     auto bf = [&](long long i) { return __uint_as_float((uint32_t)p[i] << 16); };
@@ -203,7 +285,7 @@ template <int FMT>
 __global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, int qb, int nq, int q_chunk,
                                    const double2 *__restrict__ xph, const double2 *__restrict__ xpp,
                                    const float2 *__restrict__ xph32, const float2 *__restrict__ xpp32,
-                                   double2 *__restrict__ part) {
+                                   double2 *__restrict__ part, const float *__restrict__ fsc) {
   __shared__ double2 red[8];
   const int chunk = blockIdx.x, Ql = blockIdx.y, r = blockIdx.z, Q = qb * g.n_om + Ql;
   const long long slabs = (long long)nq * g.n_om;                      // slices per channel in this pass
@@ -222,9 +304,10 @@ __global__ void chi_partial_kernel(Grid g, const void *__restrict__ fv, int ld, 
         rs = make_double2(rs.x + __shfl_xor_sync(0xffffffffu, rs.x, o), rs.y + __shfl_xor_sync(0xffffffffu, rs.y, o));
     } else {
       const float2 *X32 = (r < 2 ? xph32 : xpp32) + (long long)Q * g.n;
+      const float inv_sb = FMT == V_F16P ? 1.f / fsc[FSC_SB + r] : 1.f;
       Sum2 re, im;
       for (int kp = lane; kp < g.n; kp += 32) {
-        const float2 f = f_elem32<FMT>(fv, ps, base + (long long)k * ld + kp), x = X32[kp];
+        const float2 f = f_elem32<FMT>(fv, ps, base + (long long)k * ld + kp, inv_sb), x = X32[kp];
         re.add(fmaf(f.x, x.x, -f.y * x.y));
         im.add(fmaf(f.x, x.y, f.y * x.x));
       }
@@ -321,7 +404,15 @@ cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b) {
 }
 
 cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b) {
-  bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp, b.xph32, b.xpp32);
+  unsigned *xmax = b.vfmt == V_F16P ? (unsigned *)(b.fsc + FSC_XMAX) : nullptr;
+  bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp, b.xph32, b.xpp32, xmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_scales(cudaStream_t st, Buffers &b, const double *lam_max) {
+  Bound4 lm;
+  for (int r = 0; r < 4; ++r) lm.v[r] = (float)lam_max[r];
+  split_scales_kernel<<<1, 1, 0, st>>>(b.fsc, lm);
   return cudaGetLastError();
 }
 
@@ -397,13 +488,16 @@ cudaError_t launch_chi(cudaStream_t st, const Grid &g, Buffers &b, int qb, int n
   dim3 grid(nchunk, (unsigned)slabs, 4);
   if (b.vfmt == V_C128)
     chi_partial_kernel<V_C128><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, nullptr, nullptr,
-                                                     b.chi_part);
+                                                     b.chi_part, b.fsc);
   else if (b.vfmt == V_C64)
     chi_partial_kernel<V_C64><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.xph32, b.xpp32,
-                                                    b.chi_part);
+                                                    b.chi_part, b.fsc);
+  else if (b.vfmt == V_F16P)
+    chi_partial_kernel<V_F16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.xph32,
+                                                     b.xpp32, b.chi_part, b.fsc);
   else
     chi_partial_kernel<V_BF16P><<<grid, 256, 0, st>>>(g, b.fv, b.ld, qb, nq, b.q_chunk, b.xph, b.xpp, b.xph32,
-                                                      b.xpp32, b.chi_part);
+                                                      b.xpp32, b.chi_part, b.fsc);
   chi_sum_kernel<<<nblk(4 * slabs, 256), 256, 0, st>>>(g, qb, nq, nchunk, b.chi_part, b.chi);
   return cudaGetLastError();
 }

@@ -150,20 +150,38 @@ __device__ inline uint32_t pack_pair(float x0, float x1) {
 //
 // BF16 planes: x = h + l (+ r for F), each piece the BF16 rounding of what the previous
 // pieces leave (the differences are exact in FP32).  Plane order: Gamma X (Re h, Re l,
-// Im h, Im l), F (Re h, Im h, Re l, Im l, Re r, Im r).
-template <typename S, bool PL>
+// Im h, Im l), F (Re h, Im h, Re l, Im l, Re r, Im r).  FP16 planes: the channel's scaled
+// value x * 2^e = h + l (f16_split), planes Gamma X (Re h, Re l, Im h, Im l), F (Re h, Im h,
+// Re l, Im l).
+template <typename S, int PL>
 struct Out {
   void *gam, *fv;
   long long ps;  // plane stride in elements (PL)
-  // element o of this lane (o is even on even lanes, odd on odd lanes)
-  __device__ inline void put(long long o, float2 ga, float2 f) const {
+  // element o of this lane (o is even on even lanes, odd on odd lanes); sa, sb: the scales of
+  // Gamma X and F (FP16 planes)
+  __device__ inline void put(long long o, float2 ga, float2 f, float sa = 1.f, float sb = 1.f) const {
     const unsigned mask = __activemask();
     const bool odd = threadIdx.x & 1;
     // even lanes send Im, odd lanes send Re: each receives the partner's half it stores
     const float ga_in = __shfl_xor_sync(mask, odd ? ga.x : ga.y, 1);
     const float f_in = __shfl_xor_sync(mask, odd ? f.x : f.y, 1);
     const long long o2 = o >> 1;  // the pair's index in BF16x2 units
-    if constexpr (PL) {
+    if constexpr (PL == V_F16P) {
+      uint32_t *pg = (uint32_t *)gam, *pf = (uint32_t *)fv;
+      const long long ps2 = ps >> 1;
+      const float g0 = odd ? ga_in : ga.x, g1 = odd ? ga.y : ga_in;
+      const float f0 = odd ? f_in : f.x, f1 = odd ? f.y : f_in;
+      const int part = odd ? 1 : 0;
+      uint32_t h0, l0, h1, l1;
+      f16_split(sa * g0, h0, l0);
+      f16_split(sa * g1, h1, l1);
+      pg[(2 * part) * ps2 + o2] = h0 | (h1 << 16);
+      pg[(2 * part + 1) * ps2 + o2] = l0 | (l1 << 16);
+      f16_split(sb * f0, h0, l0);
+      f16_split(sb * f1, h1, l1);
+      pf[part * ps2 + o2] = h0 | (h1 << 16);
+      pf[(2 + part) * ps2 + o2] = l0 | (l1 << 16);
+    } else if constexpr (PL == V_BF16P) {
       uint32_t *pg = (uint32_t *)gam, *pf = (uint32_t *)fv;
       const long long ps2 = ps >> 1;
       // (element k', element k'+1) of this lane's part
@@ -185,25 +203,25 @@ struct Out {
         *reinterpret_cast<float4 *>((S *)fv + 2 * o2) = make_float4(f_x, f_in, f.x, f.y);
     }
   }
-  __device__ inline void put(long long o, double2 ga, double2 f) const {
+  __device__ inline void put(long long o, double2 ga, double2 f, float = 1.f, float = 1.f) const {
     ((S *)gam)[o] = ga;
     ((S *)fv)[o] = f;
   }
 };
 
 // S: storage type of vertices, C: arithmetic type (double2 for FP64, float2 for the split path);
-// PL: operands written as BF16 planes.
+// PL: operands written as BF16 (V_BF16P) or FP16 (V_F16P) planes, else as complex values.
 // Pass p covers the output transfers with q-momentum in [p.qb, p.qb + p.nq); the operand
 // buffers hold their 4 * nq * NOmega slices with rows of ld elements.  A fused pass (all
 // momenta) writes the d/m outputs at q and the s/t outputs at q' = k + k' + q of one gather
 // step; otherwise each target momentum takes two gather steps, one per channel pair.
-template <typename S, typename C, bool PL, bool TAB>
+template <typename S, typename C, int PL, bool TAB>
 __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__restrict__ phi, Out<S, PL> out, int ld,
                                                        const double2 *__restrict__ k1,
                                                        const double2 *__restrict__ k2row,
                                                        const C *__restrict__ xph, const C *__restrict__ xpp,
                                                        const C *__restrict__ gtab, double2 *__restrict__ dfpart,
-                                                       Lam lam, Pass pass) {
+                                                       Lam lam, Pass pass, const float *__restrict__ fsc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.n_om * g.n_nu;
   // R blocks are read along columns (map A) and anti-diagonals (map C): rows padded by two
@@ -218,6 +236,8 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
   C *FKd = (C *)(St + NB);  // K1 + K2row(k) at transfer (k'-k, m~), x = d
   C *FKm = FKd + g.n_om;
   __shared__ double2 red[256];
+  __shared__ float ssc[8];  // FP16 planes: scales of Gamma X and F per channel
+  if (PL == V_F16P && threadIdx.x < 8) ssc[threadIdx.x] = fsc[threadIdx.x < 4 ? FSC_SA + threadIdx.x : FSC_SB + threadIdx.x - 4];
 
   const int ikp = blockIdx.x, k = blockIdx.y;
   const int ik = k / g.n_nu, n = g.n_lo + k % g.n_nu;
@@ -296,8 +316,8 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
       const int Q = iq * g.n_om + mi;
       const long long o_dm = ((long long)(Q - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
       const C xq = (xph_[(long long)Q * nn + ikp * g.n_nu + npi]);
-      out.put(o_dm, cmul(Gd, xq), Fd);
-      out.put(ochan + o_dm, cmul(Gm, xq), Fm);
+      out.put(o_dm, cmul(Gd, xq), Fd, ssc[0], ssc[4]);
+      out.put(ochan + o_dm, cmul(Gm, xq), Fm, ssc[1], ssc[5]);
       // Eq. PA_Sigma, ph part: G(k+q) X_ph(Q,k') [F_d - F_m - (Lambda0_d - Lambda0_m)]
       const C gkq = (gtab[(long long)cmom * g.n_g + (n + m - g.g_lo)]);
       acc = cfma(cmul(gkq, xq), Fd - Fm - twoU, acc);
@@ -328,8 +348,8 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
       const int Qp = iqp * g.n_om + mi;
       const long long o_st = ((long long)(Qp - pass.qb * g.n_om) * nn + k) * ld + ikp * g.n_nu + npi;
       const C xqp = (xpp_[(long long)Qp * nn + ikp * g.n_nu + npi]);
-      out.put(2 * ochan + o_st, (-0.5f) * cmul(Gs, xqp), Fs);
-      out.put(3 * ochan + o_st, 0.5f * cmul(Gt, xqp), Ft);
+      out.put(2 * ochan + o_st, (-0.5f) * cmul(Gs, xqp), Fs, ssc[2], ssc[6]);
+      out.put(3 * ochan + o_st, 0.5f * cmul(Gt, xqp), Ft, ssc[3], ssc[7]);
       // pp part: G(q'-k) X_pp(Q',k') [F_s + F_t - (Lambda0_s + Lambda0_t)]
       const C gqk = (gtab[(long long)pqk * g.n_g + (m - n - 1 - g.g_lo)]);
       acc = cfma(cmul(gqk, xqp), Fs + Ft - twoU, acc);
@@ -372,7 +392,7 @@ cudaError_t launch_kernels_extract(cudaStream_t st, const Grid &g, Buffers &b, b
   return cudaGetLastError();
 }
 
-template <typename S, typename C, bool PL, bool TAB>
+template <typename S, typename C, int PL, bool TAB>
 static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, Lam lam, const Pass &p, long long ps) {
   auto kfn = assemble_kernel<S, C, PL, TAB>;
   const size_t sm = assemble_smem_bytes(g, sizeof(S) == sizeof(float2));
@@ -391,7 +411,7 @@ static cudaError_t assemble_launch(cudaStream_t st, const Grid &g, Buffers &b, L
     gtab = (const C *)b.gtab;
   }
   kfn<<<dim3(g.nk, g.n), 256, sm, st>>>(g, (const S *)b.phi, out, b.ld, b.k1, b.k2row, xph, xpp, gtab, b.dfpart, lam,
-                                        p);
+                                        p, b.fsc);
   return cudaGetLastError();
 }
 
@@ -409,15 +429,19 @@ cudaError_t launch_assemble(cudaStream_t st, const Grid &g, Buffers &b, const do
   const long long ps = 4LL * b.q_chunk * g.n_om * g.n * (long long)b.ld;
   switch (b.vfmt) {
     case V_C128:
-      return tab ? assemble_launch<double2, double2, false, true>(st, g, b, lam, p, ps)
-                 : assemble_launch<double2, double2, false, false>(st, g, b, lam, p, ps);
+      return tab ? assemble_launch<double2, double2, 0, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<double2, double2, 0, false>(st, g, b, lam, p, ps);
     case V_C64:
-      return tab ? assemble_launch<float2, float2, false, true>(st, g, b, lam, p, ps)
-                 : assemble_launch<float2, float2, false, false>(st, g, b, lam, p, ps);
+      return tab ? assemble_launch<float2, float2, 0, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<float2, float2, 0, false>(st, g, b, lam, p, ps);
+    case V_F16P:
+      if (b.assembly == 0 && assemble_tiled_ok(g)) return launch_assemble_tiled(st, g, b, lam, p, ps, tab);
+      return tab ? assemble_launch<float2, float2, V_F16P, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<float2, float2, V_F16P, false>(st, g, b, lam, p, ps);
     default:
       if (b.assembly == 0 && assemble_tiled_ok(g)) return launch_assemble_tiled(st, g, b, lam, p, ps, tab);
-      return tab ? assemble_launch<float2, float2, true, true>(st, g, b, lam, p, ps)
-                 : assemble_launch<float2, float2, true, false>(st, g, b, lam, p, ps);
+      return tab ? assemble_launch<float2, float2, V_BF16P, true>(st, g, b, lam, p, ps)
+                 : assemble_launch<float2, float2, V_BF16P, false>(st, g, b, lam, p, ps);
   }
 }
 

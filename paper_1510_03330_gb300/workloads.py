@@ -25,6 +25,7 @@ FP64 = "fp64"
 SPLIT_TF32X3 = "split_tf32x3"
 SPLIT_BF16X3 = "split_bf16x3"
 SPLIT_BF16X6 = "split_bf16x6"
+SPLIT_FP16X3 = "split_fp16x3"
 
 
 @dataclass(frozen=True)
@@ -118,12 +119,14 @@ def batch_draw(seed: int = 1510, count: int = 64) -> list[Params]:
     return out
 
 
-def device_bytes_bf16x3(p: Params) -> int:
-    """Device memory of a single-pass PQ_SPLIT_BF16X3 solve: Phi (complex64, 8 bytes per element)
-    and the BSE operand planes (8 + 12 bytes per element; rows padded to 8 elements), plus the
-    one-particle and self-energy tables (bounded by 128 MB at the default quadrature)."""
+def device_bytes_planes(p: Params, precision: str = SPLIT_FP16X3) -> int:
+    """Device memory of a single-pass solve with operand planes: Phi (complex64, 8 bytes per
+    element) and the BSE operand planes (Gamma X 8 bytes, F 8 bytes for FP16x3 or 12 for BF16x3
+    per element; rows padded to 8 elements), plus the one-particle and self-energy tables
+    (bounded by 128 MB at the default quadrature)."""
     ld = (p.n + 7) // 8 * 8
-    return 4 * p.n_Q * p.n * (8 * p.n + 20 * ld) + (128 << 20)
+    ops = 16 if precision == SPLIT_FP16X3 else 20
+    return 4 * p.n_Q * p.n * (8 * p.n + ops * ld) + (128 << 20)
 
 
 def random_state(p: Params, seed: int, amplitude: float | None = None):

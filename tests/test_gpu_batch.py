@@ -6,7 +6,9 @@ import numpy as np
 import pytest
 
 from oracle import parquet_oracle as O
-from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, Params
+from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, SPLIT_FP16X3, Params
+
+PLANE = {SPLIT_FP16X3: (1e-6, 2e-6), SPLIT_BF16X3: (5e-6, 1.5e-5)}
 
 pytestmark = pytest.mark.gpu
 
@@ -37,15 +39,16 @@ def all_phi(s, p):
     return np.stack([np.stack([s.Phi(r, Q) for Q in range(p.n_Q)]) for r in range(4)])
 
 
+@pytest.mark.parametrize("precision", list(PLANE))
 @pytest.mark.parametrize("tile_cols,order", [(0, -1), (64, 1), (128, 0)])
-def test_batch_members_follow_their_own_iteration(tile_cols, order):
+def test_batch_members_follow_their_own_iteration(tile_cols, order, precision):
     from paper_1510_03330_gb300.binding import Batch, Solver
 
     iters = 6  # with tuning: four candidate iterations, then the captured graph
-    alone = [Solver(p, precision=SPLIT_BF16X3) for p in MEMBERS]
+    alone = [Solver(p, precision=precision) for p in MEMBERS]
     for s in alone:
         s.iterate(iters)
-    mem = [Solver(p, precision=SPLIT_BF16X3) for p in MEMBERS]
+    mem = [Solver(p, precision=precision) for p in MEMBERS]
     with Batch(mem, tile_cols=tile_cols, order=order, time_steps=True) as b:
         for _ in range(iters):
             d = b.iterate(1)
@@ -66,21 +69,23 @@ def test_batch_members_follow_their_own_iteration(tile_cols, order):
         s.close()
 
 
-def test_batch_member_matches_oracle():
+@pytest.mark.parametrize("precision", list(PLANE))
+def test_batch_member_matches_oracle(precision):
     from paper_1510_03330_gb300.binding import Batch, Solver
 
+    tol, tol_phi = PLANE[precision]
     p = MEMBERS[1]
     st = O.zero_state(p)
-    mem = [Solver(q, precision=SPLIT_BF16X3) for q in MEMBERS]
+    mem = [Solver(q, precision=precision) for q in MEMBERS]
     with Batch(mem) as b:
         for it in range(3):
             res = O.iterate(p, st)
             st = res.state
             b.iterate(1)
-        assert rel(mem[1].sigma(), st.sigma) < 5e-5
-        assert rel(all_phi(mem[1], p), st.phi) < 3e-4
+        assert rel(mem[1].sigma(), st.sigma) < tol
+        assert rel(all_phi(mem[1], p), st.phi) < tol_phi
         chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
-        assert rel(mem[1].chi(1), chi[1]) < 5e-5
+        assert rel(mem[1].chi(1), chi[1]) < tol
     for s in mem:
         s.close()
 
@@ -93,7 +98,9 @@ def test_batch_refusals():
         Batch([f])
     with Solver(MEMBERS[1], precision=SPLIT_BF16X3, q_chunk=2) as c, pytest.raises(ParquetError):
         Batch([c])  # several passes per iteration
-    s = Solver(p, precision=SPLIT_BF16X3)
+    with Solver(p, precision=SPLIT_BF16X3) as x, Solver(p, precision=SPLIT_FP16X3) as y, pytest.raises(ParquetError):
+        Batch([x, y])  # one operand format per batch
+    s = Solver(p, precision=SPLIT_FP16X3)
     b = Batch([s])
     with pytest.raises(ParquetError):
         s.iterate(1)  # the batch owns the iteration

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import parquet_oracle as O
-from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, Params, random_state
+from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, SPLIT_FP16X3, Params, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +36,7 @@ def all_phi(s, p):
     return np.stack([np.stack([s.Phi(r, Q) for Q in range(p.n_Q)]) for r in range(4)])
 
 
-@pytest.mark.parametrize("precision,tol,tol_phi", [(FP64, 1e-10, 1e-10), (SPLIT_BF16X3, 5e-5, 3e-4)])
+@pytest.mark.parametrize("precision,tol,tol_phi", [(FP64, 1e-10, 1e-10), (SPLIT_FP16X3, 1e-6, 2e-6), (SPLIT_BF16X3, 5e-6, 1.5e-5)])
 @pytest.mark.parametrize("variant", [dict(kernel_level=1), dict(edge_rule="lower"),
                                      dict(kernel_level=1, edge_rule="lower"), dict(sde="truncated")])
 def test_kernel_ablation_matches_oracle(precision, tol, tol_phi, variant):

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import parquet_oracle as O
-from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, Params
+from paper_1510_03330_gb300.workloads import FP64, SPLIT_BF16X3, SPLIT_FP16X3, Params
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def tables(p, nl, seed=11):
     return {r: (0.3 * p.U * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)), nl) for r in range(4)}
 
 
-@pytest.mark.parametrize("precision,tol,tol_phi", [(FP64, 1e-10, 1e-10), (SPLIT_BF16X3, 5e-5, 3e-4)])
+@pytest.mark.parametrize("precision,tol,tol_phi", [(FP64, 1e-10, 1e-10), (SPLIT_FP16X3, 1e-6, 2e-6), (SPLIT_BF16X3, 5e-6, 1.5e-5)])
 def test_tabulated_lambda_matches_oracle(precision, tol, tol_phi):
     from paper_1510_03330_gb300.binding import Solver
 

@@ -144,17 +144,26 @@ def test_split_tf32x3_iterations_match_oracle(name):
     assert max(v for k, v in errs.items() if k.startswith("phi")) < 5 * TOL_SPLIT, errs
 
 
-@pytest.mark.parametrize("name", ["square_2x2_nu8_om8", "square_3x3_nu16_om8", "square_1x1_nu6_om5"])
-def test_split_bf16x3_iterations_match_oracle(name):
-    """BF16x3 split path against the FP64 oracle: BF16 hi/lo operands keep ~2^-16
-    per product, so Sigma, F and chi are checked within 5e-5, Phi within 3e-4."""
+# Tolerances of the plane formats on the small shapes (max-norm relative error of Sigma, F and
+# chi; of the raw product Phi, whose k''-sums cancel, in the second entry): FP16x3 keeps 2^-22
+# per product and its accumulation in chunks, the benchmark spec's bound of 1e-6; BF16x3 keeps
+# 2^-16 per product, which is not averaged down at these sizes (measured up to 2.3e-6 on F).
+PLANE_TOL = {"split_fp16x3": (TOL_SPLIT, 2 * TOL_SPLIT), "split_bf16x3": (5 * TOL_SPLIT, 1.5e-5)}
+
+
+@pytest.mark.parametrize("precision", list(PLANE_TOL))
+@pytest.mark.parametrize("name", list(CASES))
+def test_split_planes_iterations_match_oracle(name, precision):
+    """Plane-format split paths (the assembly writes FP16 or BF16 operand planes, the TMA-fed
+    tensor-core products read them) against the FP64 oracle: three iterations from zero and
+    one from a seeded state with stripes; Sigma, F and chi of all four channels."""
     from paper_1510_03330_gb300.binding import Solver
-    from paper_1510_03330_gb300.workloads import SPLIT_BF16X3
 
     p = CASES[name]
+    tol, tol_phi = PLANE_TOL[precision]
     st = O.zero_state(p)
     errs = {}
-    with Solver(p, precision=SPLIT_BF16X3) as s:
+    with Solver(p, precision=precision) as s:
         for it in range(3):
             res = O.iterate(p, st)
             st = res.state
@@ -163,10 +172,19 @@ def test_split_bf16x3_iterations_match_oracle(name):
         errs["phi"] = rel(all_slices(s, s.Phi, p), st.phi)
         errs["F"] = rel(all_slices(s, s.F, p), res.F)
         chi = O.susceptibility(res.F, res.X_ph, res.X_pp)
-        errs["chi_m"] = rel(s.chi(1), chi[1])
-    print(name, errs)
-    assert max(v for k, v in errs.items() if k != "phi") < 5e-5, errs
-    assert errs["phi"] < 3e-4, errs
+        for r in range(4):
+            errs[f"chi{r}"] = rel(s.chi(r), chi[r])
+    phi, sig = random_state(p, seed=1510)
+    res = O.iterate(p, O.State(phi, sig))
+    with Solver(p, precision=precision) as s:
+        s.set_state(phi, sig)
+        s.iterate(1)
+        errs["sigma_rand"] = rel(s.sigma(), res.state.sigma)
+        errs["phi_rand"] = rel(all_slices(s, s.Phi, p), res.state.phi)
+        errs["F_rand"] = rel(all_slices(s, s.F, p), res.F)
+    print(name, precision, errs)
+    assert max(v for k, v in errs.items() if not k.startswith("phi")) < tol, errs
+    assert max(v for k, v in errs.items() if k.startswith("phi")) < tol_phi, errs
 
 
 def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
@@ -197,16 +215,16 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
 
 @pytest.mark.parametrize("name,precision,tol,tol_F,tol_phi", [
     ("square4_u2_b5", "fp64", TOL_FP64, TOL_FP64, TOL_FP64),
-    # n = 1024: the tensor cores' FP32 accumulation truncates over ~768 updates per element,
-    # a bias of a few 1e-6 on Phi and F (Sigma keeps 1e-6): the bounds below are the measured
-    # ones, above the 1e-6 target for F and Phi
-    ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 3 * TOL_SPLIT, 15 * TOL_SPLIT),
-    # the default scheme (BF16 operands, half as many accumulator updates per k): Sigma and F
-    # within the 1e-6 target; Phi, the raw product, at the TF32x3 bound
-    ("square8_u2_b4", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT),
+    # n = 1024 with TF32 pieces: one FP32 accumulator per tile over the whole k range (the
+    # kernel of the complex64 operands), measured bounds above the 1e-6 target for F and Phi
+    ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 5 * TOL_SPLIT, 15 * TOL_SPLIT),
+    # FP16 planes, chunked accumulation: the benchmark spec's bound on Sigma, F and chi, every channel
+    ("square8_u2_b4", "split_fp16x3", TOL_SPLIT, TOL_SPLIT, 2 * TOL_SPLIT),
+    # BF16 planes (2^-16 per product), chunked accumulation
+    ("square8_u2_b4", "split_bf16x3", TOL_SPLIT, 3 * TOL_SPLIT, 15 * TOL_SPLIT),
     # the large solve (n = 1536, 116 GB of Phi): several passes over the q-momenta, so F is
     # kept for the last pass only and is checked on the sampled slices that fall in it
-    ("square8_u3_b8_nu24", "split_bf16x3", TOL_SPLIT, TOL_SPLIT, 15 * TOL_SPLIT)])
+    ("square8_u3_b8_nu24", "split_fp16x3", TOL_SPLIT, TOL_SPLIT, 2 * TOL_SPLIT)])
 def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
     """The benchmark workloads at full size, in the launch configuration bench.py
     times: iterations 1 and 2 from the zero state, compared on sampled transfer
@@ -236,24 +254,30 @@ def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
         s.iterate(1)
         gpu1 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs}, "F": kept_F(s)}
         s.iterate(1)
-        gpu2 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs}, "F": kept_F(s)}
+        gpu2 = {"sigma": s.sigma(), "phi": {Q: [s.Phi(r, Q) for r in range(4)] for Q in Qs}, "F": kept_F(s),
+                "chi": [s.chi(r) for r in range(4)]}
     a = p.mix
     # iteration 1 from the zero state
     zero = np.broadcast_to(np.zeros((), complex), shape)
     sig0 = np.zeros((p.n_k, p.n_ext), complex)
     phi1, F1, sig1, s1, X_ph, X_pp = _oracle_sampled_iteration(p, zero, sig0, Qs, outs)
 
-    def check(gpu, refs, bound, what):
-        # max-norm error over the sampled slices, relative to the vertex's max |ref| over the
-        # four channels (Psi_t, a difference of channels, is far smaller than the others)
-        scale = max(np.abs(refs[i][r]).max() for i in range(len(Qs)) for r in range(4))
+    def check(gpu, refs, bound, what, per_channel):
+        # max-norm error over the sampled slices, relative to the channel's own max |ref| (F),
+        # or to the vertex's max |ref| over the four channels (Phi: Psi_t, a difference of
+        # channels, is far smaller than the others at the first iterations)
+        vscale = max(np.abs(refs[i][r]).max() for i in range(len(Qs)) for r in range(4))
         for r in range(4):
-            err = max(np.abs(gpu[Q][r] - refs[i][r]).max() for i, Q in enumerate(Qs) if Q in gpu)
+            kept = [(i, Q) for i, Q in enumerate(Qs) if Q in gpu]
+            scale = max(np.abs(refs[i][r]).max() for i, _ in kept) if per_channel else vscale
+            if scale == 0.0:  # Psi_t of the first iterate vanishes identically
+                scale = vscale
+            err = max(np.abs(gpu[Q][r] - refs[i][r]).max() for i, Q in kept)
             print(what, r, err / scale)
             assert err <= bound * scale + 1e-300, (what, r, err, scale)
 
-    check(gpu1["phi"], [[a * phi1[r, i] for r in range(4)] for i in range(len(Qs))], tol_phi, "phi1")
-    check(gpu1["F"], [[F1[r, i] for r in range(4)] for i in range(len(Qs))], tol_F, "F1")
+    check(gpu1["phi"], [[a * phi1[r, i] for r in range(4)] for i in range(len(Qs))], tol_phi, "phi1", False)
+    check(gpu1["F"], [[F1[r, i] for r in range(4)] for i in range(len(Qs))], tol_F, "F1", True)
     for (ik, n), v in sig1.items():
         assert abs(gpu1["sigma"][ik, n - g.e_lo] - a * v) <= tol * np.abs(a * s1).max()
     # the first iterate: Sigma~2 and dF vanish (K = 0, F = Lambda), Phi is constant per (r, Q)
@@ -269,8 +293,16 @@ def test_full_size_sampled_parity(name, precision, tol, tol_F, tol_phi):
         ref = a * v + (1 - a) * sig_state[ik, n - g.e_lo]
         assert abs(gpu2["sigma"][ik, n - g.e_lo] - ref) <= tol * scale
     check(gpu2["phi"], [[a * phi2[r, i] + (1 - a) * phi_state[r, Q] for r in range(4)] for i, Q in enumerate(Qs)],
-          tol_phi, "phi2")
-    check(gpu2["F"], [[F2[r, i] for r in range(4)] for i in range(len(Qs))], tol_F, "F2")
+          tol_phi, "phi2", False)
+    check(gpu2["F"], [[F2[r, i] for r in range(4)] for i in range(len(Qs))], tol_F, "F2", True)
+    # chi of the second iteration at the sampled transfers, all four channels (App. A, "Notations")
+    X2 = O.bubbles(g, O.Propagator(g, sig_state))
+    for r in range(4):
+        X = (X2[0] if r < 2 else X2[1])[Qs]
+        ref = -X.sum(axis=1) - np.einsum("qk,qkl,ql->q", X, F2[r], X)
+        err = np.abs(gpu2["chi"][r][Qs] - ref).max() / np.abs(ref).max()
+        print("chi2", r, err)
+        assert err <= tol, ("chi", r, err)
 
 
 def test_nonfinite_self_energy_is_reported_and_poisons_the_context():
