@@ -315,7 +315,8 @@ def run_batch(a, world, barrier, clk_factory):
                 s_.iterate(1)
         e1.record(stream)
         torch.cuda.synchronize()
-        seq_ms += e0.elapsed_time(e1)
+        wave_seq = e0.elapsed_time(e1)
+        seq_ms += wave_seq
         b = Batch(sols, time_steps=True)
         b.iterate(a.warmup + 4)  # the first iterations tune the grouped launch, then the graph is captured
         torch.cuda.synchronize()
@@ -328,9 +329,12 @@ def run_batch(a, world, barrier, clk_factory):
             bse += b.times()["bse"]
         f1.record(stream)
         torch.cuda.synchronize()
-        bat_ms += f0.elapsed_time(f1)
+        wave_bat = f0.elapsed_time(f1)
+        bat_ms += wave_bat
         bse_ms += bse
-        tuned.append(dict(b.config(), solves=len(w)))
+        tuned.append(dict(b.config(), solves=len(w), max_n=max(draw[i].n for i in w),
+                          one_at_a_time_ms=wave_seq / a.steps, batched_ms=wave_bat / a.steps,
+                          batched_over_one_at_a_time=wave_seq / wave_bat))
         b.close()
         for s_ in sols:
             s_.close()

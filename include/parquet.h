@@ -72,9 +72,9 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
  *   PQ_SPLIT_FP16X3: the same with FP16 planes of each channel's operands
  *     scaled by a power of two (chosen every iteration from bounds of the
  *     vertex and the bubbles, so every piece lies in the FP16 range): 11-bit
- *     pieces, ~2^-22 per product at the cost of BF16x3, and the products are
- *     accumulated in chunks of 256 k that are summed in FP32 registers, so the
- *     accumulation error does not grow with n;
+ *     pieces, ~2^-22 per product at the cost of BF16x3;
+ *   both plane formats accumulate the products in chunks of 512 k that are summed
+ *   in FP32 registers, so the accumulation error does not grow with n;
  *   PQ_SPLIT_BF16X6 is rejected by pq_init with PQ_EINVAL. */
 typedef enum {
   PQ_FP64 = 0,
@@ -117,14 +117,18 @@ typedef struct {
    * Sigma~1 + Sigma~2 + the box sum of F - F~); 1 Eq. PA_Sigma summed on the vertex box
    * with the vertex cut off at its boundary (zero outside the box), for comparison. */
   int sde;
-  /* Complex output columns per tile of the tensor-core products of the plane formats: 0
-   * (default) 64 for FP16x3 (chunked accumulation) and 128 for BF16x3; 64 or 128 to choose.
-   * FP16x3 accumulates in chunks only with 64-column tiles. */
+  /* Complex output columns per tile of the tensor-core products of the plane formats
+   * (BF16x3, FP16x3): 0 (default) or 128, or 64 (narrower tiles, more operand traffic per
+   * flop: slower on large matrices). */
   int bse_tile_cols;
   /* Divergence detection in pq_iterate: when max |dSigma| has grown in each of the last
    * diverge_window iterations, stop with PQ_EDIVERGED (the iteration that diverges is kept:
    * the state is valid, e.g. for a restart with stronger mixing).  0 (default): off. */
   int diverge_window;
+  /* Filling: 0 (default) keeps mu fixed; a value in (0, 2) (square lattice) is the number of
+   * electrons per site (both spins) to hold: every iteration first sets mu, by a Newton search
+   * on the FP64 density of the state's G (pq_density), then runs at that mu (pq_get_mu). */
+  double target_density;
   void *cuda_stream;      /* cudaStream_t for all work; NULL = legacy default stream */
   /* Optional device allocator: returns 256-byte aligned device memory or NULL.
    * When NULL, cudaMalloc/cudaFree are used. */
@@ -166,12 +170,17 @@ PQ_API pq_status pq_set_Lambda(pq_ctx *ctx, int channel, const double *host_c128
 PQ_API pq_status pq_iterate(pq_ctx *ctx, int max_iter, double tol, int *iters_done,
                      double *last_max_dsigma);
 
-/* Self-energy of the current state, host c128 [L*L][n_ext]; len = number of
- * doubles available in out (>= 2*L*L*n_ext). */
+/* Self-energy of the current state (the mixed Sigma of the regulated
+ * Schwinger-Dyson equation, Sec. II.B and App. A Eq. PA_Sigma, that enters the
+ * Dyson equation Eq. PA_Dyson of the next iteration), host c128 [L*L][n_ext];
+ * len = number of doubles available in out (>= 2*L*L*n_ext). */
 PQ_API pq_status pq_get_Sigma(const pq_ctx *ctx, double *out, size_t len);
 
-/* Full vertex F_r(Q) of the last iteration (the one assembled from the state
- * that iteration started from), host c128 [n][n], n = L*L*Nnu. */
+/* Full vertex F_r(Q) = Gamma_r(Q) + Phi_r(Q) of the last iteration (Eq. PA_F with
+ * the parquet equations App. A Eqs. PA_Gamma_dm, PA_Gamma_st, assembled from the
+ * state that iteration started from; the right factor of its Bethe-Salpeter
+ * equation, Eq. PA_F_Phi), host c128 [n][n], n = L*L*Nnu.  The split paths
+ * return the operand they multiplied (FP16x3: (h + l) / 2^e, to 2^-22). */
 PQ_API pq_status pq_get_F(const pq_ctx *ctx, int channel, int Q, double *out, size_t len);
 
 /* Reducible vertex Phi_r(Q) of the current state, host c128 [n][n]. */
@@ -194,6 +203,18 @@ PQ_API pq_status pq_sigma_second_order(pq_ctx *ctx, const double *sigma_c128, do
  * storage precision) and Sigma as host c128 [L*L][n_ext]; either may be NULL
  * to keep it. */
 PQ_API pq_status pq_set_state(pq_ctx *ctx, const double *phi_c128, const double *sigma_c128);
+
+/* Electron density per site (both spins) of G = [i nu + mu - eps_k - Sigma(k)]^-1 (App. A,
+ * Eq. PA_Dyson) for the current Sigma and mu, square lattice:
+ * n = (2T/N) sum_k sum_nu G(k, i nu) e^{i nu 0+}, summed in FP64 on the device over
+ * n in [-M, M-1] (M = tau_matsubara) with the 1/(i nu) and 1/(i nu)^2 tails of G summed in
+ * closed form (1/2 and -beta (eps_k - mu)/4 per spin).  mu is the Hartree-shifted chemical
+ * potential of the solve (mu = 0 at half filling).  PQ_EINVAL on the Bethe lattice. */
+PQ_API pq_status pq_density(pq_ctx *ctx, double *n_out);
+
+/* The chemical potential of the last iteration (the one pq_init set, unless target_density
+ * moves it). */
+PQ_API pq_status pq_get_mu(const pq_ctx *ctx, double *mu_out);
 
 /* Sizes: out[0..7] = L*L, n, N_Q, n_ext, Nnu, NOmega, bytes of device memory
  * held, storage bytes per complex vertex element. */

@@ -41,7 +41,8 @@ the design notes):
 
 Every function is pinned by the tests (closed forms, limits, invariants, stored
 closed-form values); chi in all four channels by its first-order expansion at
-the first-iteration vertex.
+the first-iteration vertex; the density by the Fermi-function sum of the free
+lattice and particle-hole symmetry.
 
 Array layout: Phi[r, Q, k, k'] with r in (d, m, s, t), Q = iq*NOmega + (m-m_lo),
 k = ik*Nnu + (n-n_lo); Sigma[ik, n-e_lo] on the extended range.
@@ -538,6 +539,7 @@ class IterationResult:
     phi_new: np.ndarray
     max_dsigma: float
     K: tuple
+    mu: float = 0.0
 
 
 def zero_state(p) -> State:
@@ -546,7 +548,11 @@ def zero_state(p) -> State:
 
 def iterate(p, state: State, lam=None) -> IterationResult:
     """One Jacobi parquet iteration from (Phi, Sigma) (Sec. II): Dyson, bubbles,
-    kernel functions, parquet equations, regulated Schwinger-Dyson, BSE, mixing."""
+    kernel functions, parquet equations, regulated Schwinger-Dyson, BSE, mixing.
+    With p.density > 0 the chemical potential is first set so that the state's G holds
+    that many electrons per site (find_mu); the result's params carry it."""
+    if getattr(p, "density", 0.0) > 0.0:
+        p = p.with_(mu=find_mu(p, state.sigma, p.density), density=0.0)
     g = make_grid(p)
     lam = lambda0(p.U) if lam is None else lam
     G = Propagator(g, state.sigma)
@@ -564,7 +570,47 @@ def iterate(p, state: State, lam=None) -> IterationResult:
     a = p.mix
     nxt = State(a * phi_new + (1 - a) * state.phi, a * sigma_new + (1 - a) * state.sigma)
     dmax = float(np.abs(sigma_new - state.sigma).max())
-    return IterationResult(nxt, gamma, F, X_ph, X_pp, sigma_new, phi_new, dmax, K)
+    return IterationResult(nxt, gamma, F, X_ph, X_pp, sigma_new, phi_new, dmax, K, p.mu)
+
+
+def density(p, sigma):
+    """Electron density per site (both spins) of G = [i nu + mu - eps_k - Sigma(k)]^-1 with the
+    state's Sigma (App. A, Eq. PA_Dyson; square lattice):
+    n = (2T/N) sum_k sum_nu G(k, i nu) e^{i nu 0+}.  The 1/(i nu) and 1/(i nu)^2 tails are summed
+    in closed form (T sum_nu e^{i nu 0+}/(i nu) = 1/2, T sum_nu 1/(i nu)^2 = -beta/4), the rest
+    over n in [-M, M-1] with M = tau_matsubara (its terms fall off as 1/nu^3 and cancel pairwise
+    to leading order)."""
+    g = make_grid(p)
+    if p.lattice != "square":
+        raise ValueError("the density is defined for the lattice solve (the Bethe solve has a fixed G0)")
+    c1 = sigma_tail_c1(g, sigma)
+    M = p.tau_matsubara
+    n = np.arange(-M, M)
+    iv = 1j * g.nu(n)
+    ik = np.arange(g.nk)[:, None]
+    G = green(g, sigma, c1, ik, n[None, :])
+    c2 = (g.eps - p.mu)[:, None]
+    rest = (G - 1.0 / iv[None, :] - c2 / iv[None, :] ** 2).sum(axis=1).real * g.T
+    per_spin = 0.5 - c2[:, 0] * p.beta / 4.0 + rest
+    return float(2.0 * per_spin.mean())
+
+
+def find_mu(p, sigma, n_target, tol=1e-13, lo=-20.0, hi=20.0):
+    """Chemical potential with density(mu) = n_target at fixed Sigma, by bisection (n(mu) is
+    increasing); mu is the Hartree-shifted one of the solve (mu = 0 at half filling)."""
+    f = lambda mu: density(p.with_(mu=mu), sigma) - n_target  # noqa: E731
+    a, b = lo, hi
+    fa = f(a)
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        fm = f(m)
+        if (fm > 0) == (fa > 0):
+            a, fa = m, fm
+        else:
+            b = m
+        if b - a < tol:
+            break
+    return 0.5 * (a + b)
 
 
 def susceptibility(F, X_ph, X_pp):

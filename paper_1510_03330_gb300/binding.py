@@ -45,6 +45,7 @@ class Options(C.Structure):
         ("sde", C.c_int),
         ("bse_tile_cols", C.c_int),
         ("diverge_window", C.c_int),
+        ("target_density", C.c_double),
         ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -97,6 +98,10 @@ def load_library(path: str = LIB_PATH):
     lib.pq_sigma_second_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
     lib.pq_sigma_second_order_noalloc.restype = C.c_int
+    lib.pq_density.argtypes = [P, D]
+    lib.pq_density.restype = C.c_int
+    lib.pq_get_mu.argtypes = [P, D]
+    lib.pq_get_mu.restype = C.c_int
     lib.pq_selftest_wait_timeout.argtypes = [P, C.c_int]
     lib.pq_selftest_wait_timeout.restype = C.c_int
     lib.pq_set_state.argtypes = [P, D, D]
@@ -186,6 +191,7 @@ class Solver:
         o.sde = {"regulated": 0, "truncated": 1}[p.sde]
         o.bse_tile_cols = bse_tile_cols
         o.diverge_window = diverge_window
+        o.target_density = p.density
         self.last_status = PQ_OK
         self._alloc = None
         if use_torch:
@@ -243,6 +249,18 @@ class Solver:
                          (PQ_OK, PQ_ENOTCONV, PQ_EDIVERGED))
         self.last_status = st
         return it.value, d.value, st == PQ_OK
+
+    def density(self) -> float:
+        """Electrons per site (both spins) of the current state's G (pq_density)."""
+        v = C.c_double(0.0)
+        self._check(self.lib.pq_density(self.h, C.byref(v)))
+        return v.value
+
+    def mu(self) -> float:
+        """Chemical potential of the last iteration (pq_get_mu)."""
+        v = C.c_double(0.0)
+        self._check(self.lib.pq_get_mu(self.h, C.byref(v)))
+        return v.value
 
     def selftest_wait_timeout(self, limit_ms: int) -> int:
         """pq_selftest_wait_timeout: a device wait on a barrier nothing arrives at gives up after

@@ -127,6 +127,51 @@ __global__ void phi_from_c128(float2 *dst, const double2 *src, long long n) {
   if (i < n) dst[i] = make_float2((float)src[i].x, (float)src[i].y);
 }
 
+// Density per site (both spins) of the state's G at chemical potential mu, and d n / d mu
+// (square lattice): the device sums the Matsubara remainders, the closed-form tails are added
+// here.  Synchronous.
+pq_status density_at(pq_ctx *c, double mu, double *n, double *dn) {
+  Grid g = c->g;
+  g.mu = mu;
+  double *out = c->b.scal + 6;
+  CK(pq::launch_tail_c1(c->st, g, c->b.sigma, c->b.scal + 3));
+  CK(pq::launch_density(c->st, g, c->z.M, c->b.sigma, c->b.scal + 3, out));
+  double h[2];
+  CK(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double sum_c2 = 0.0;  // sum_k (eps_k - mu)
+  for (int ik = 0; ik < g.nk; ++ik) {
+    const int ix = ik / g.L, iy = ik % g.L;
+    sum_c2 += -2.0 * g.hop * (std::cos(2.0 * M_PI * ix / g.L) + std::cos(2.0 * M_PI * iy / g.L)) - mu;
+  }
+  *n = (2.0 / g.nk) * (0.5 * g.nk - g.beta * sum_c2 / 4.0) + 2.0 * g.T / g.nk * h[0];
+  *dn = 0.5 * g.beta + 2.0 * g.T / g.nk * h[1];
+  return PQ_OK;
+}
+
+// Chemical potential that gives the state's G the target density: Newton steps on n(mu), kept
+// inside a bracket that bisection shrinks whenever a step leaves it (n increases with mu).
+pq_status find_mu(pq_ctx *c, double target, double *mu_out) {
+  double lo = -20.0 * std::max(1.0, std::fabs(c->g.hop)) - 10.0 * std::fabs(c->g.U), hi = -lo;
+  double mu = c->g.mu, n = 0.0, dn = 0.0;
+  for (int it = 0; it < 100; ++it) {
+    pq_status s = density_at(c, mu, &n, &dn);
+    if (s != PQ_OK) return s;
+    const double f = n - target;
+    if (std::fabs(f) < 1e-14 * std::max(1.0, target)) break;
+    if (f > 0) hi = mu;
+    else lo = mu;
+    double next = dn > 0 ? mu - f / dn : 0.5 * (lo + hi);
+    if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+    if (hi - lo < 1e-15 * std::max(1.0, std::fabs(mu))) break;
+    mu = next;
+  }
+  if (!std::isfinite(n) || std::fabs(n - target) > 1e-9)
+    return fail(c, PQ_ENOTCONV, "mu search: density %.15g instead of %.15g", n, target);
+  *mu_out = mu;
+  return PQ_OK;
+}
+
 // Device work of one iteration, queued on the context's stream without waiting.  With
 // bse == false the products of a single-pass iteration are left out (a batch runs them in
 // its grouped launch); timing records the step events.
@@ -140,6 +185,13 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
   auto mark = [&](int i) {
     if (tm) cudaEventRecord(c->ev[i], st);
   };
+  if (c->opt.target_density > 0.0) {
+    // fixed density: mu for the state's Sigma, then the iteration at that mu
+    double mu = g.mu;
+    pq_status s = find_mu(c, c->opt.target_density, &mu);
+    if (s != PQ_OK) return s;
+    g.mu = mu;
+  }
   mark(0);
   CK(pq::launch_tail_and_green(st, g, b));
   mark(1);
@@ -332,6 +384,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
   if (o.bse_tile_cols != 0 && o.bse_tile_cols != 64 && o.bse_tile_cols != 128)
     return fail(nullptr, PQ_EINVAL, "bse_tile_cols must be 0, 64 or 128");
   if (o.diverge_window < 0) return fail(nullptr, PQ_EINVAL, "diverge_window must be >= 0");
+  if (o.target_density < 0.0 || o.target_density >= 2.0 || (o.target_density > 0.0 && lattice != PQ_SQUARE))
+    return fail(nullptr, PQ_EINVAL, "target_density must be 0 (fixed mu) or in (0, 2) on the square lattice");
 
   pq_ctx *c = new pq_ctx();
   c->opt = o;
@@ -387,8 +441,7 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
            : o.precision == PQ_SPLIT_FP16X3  ? pq::V_F16P
                                              : pq::V_BF16P;
   b.ld = pq::split_planes(b.vfmt) ? (g.n + 7) / 8 * 8 : g.n;  // TMA rows: multiples of 16 bytes
-  // BSE tile: 64 complex columns for FP16 planes (chunked accumulation), else 128
-  c->bse_cols = o.bse_tile_cols ? o.bse_tile_cols : (b.vfmt == pq::V_F16P ? 64 : 128);
+  c->bse_cols = o.bse_tile_cols ? o.bse_tile_cols : 128;  // complex columns per tile of the products
   if (o.q_chunk < 0) {
     delete c;
     return fail(nullptr, PQ_EINVAL, "q_chunk must be >= 0");
@@ -830,6 +883,20 @@ pq_status pq_set_state(pq_ctx *c, const double *phi, const double *sigma) {
       }
     }
   }
+  return PQ_OK;
+}
+
+pq_status pq_density(pq_ctx *c, double *n_out) {
+  if (!c || !n_out) return PQ_EINVAL;
+  if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned");
+  if (c->g.lattice != PQ_SQUARE) return fail(c, PQ_EINVAL, "the density is defined for the square lattice");
+  double dn = 0.0;
+  return density_at(c, c->g.mu, n_out, &dn);
+}
+
+pq_status pq_get_mu(const pq_ctx *c, double *mu) {
+  if (!c || !mu) return PQ_EINVAL;
+  *mu = c->g.mu;
   return PQ_OK;
 }
 

@@ -2,7 +2,10 @@
 // tiled BF16 kernel in pq_assemble_tiled.cu).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+
+#include <cuda_fp16.h>
 
 #include "pq_common.cuh"
 
@@ -38,40 +41,29 @@ __device__ inline uint32_t bf16_round(float x) {
   return u + 0x7FFFu + ((u >> 16) & 1u);
 }
 
-// FP16 pieces of a scaled value y (|y| <= 2^15), in FP32 and integer arithmetic only (the
-// conversion unit is narrow on this part).  Veltkamp's splitting (Dekker 1971): with
-// c = (2^13 + 1) y, the difference c - (c - y) is y rounded to its 11 leading bits, and the
-// remainder y - hi is exact in FP32.  y = h + l with h and l such 11-bit values; both fit
-// FP16 (11-bit significand), so their bit patterns follow by rebiasing the exponent.
-// Pieces below 2^-14 (the FP16 normal range) are flushed to zero: the representation error
-// is at most 2^-22 |y| + 2^-14, i.e. below 2^-29 of the scale 2^15 the values are mapped to.
-// The intrinsics keep the compiler from contracting the split into an FMA.
-__device__ inline float f16_lead(float y) {
-  const float c = __fmul_rn(y, 8193.0f);
-  return __fsub_rn(c, __fsub_rn(c, y));
+// FP16 pieces of two scaled values y0, y1 (|y| <= 2^15), packed as FP16x2 words with y0 in the
+// low half: h = fp16(y) rounded to nearest, l = fp16(y - h).  y - h is exact in FP32 (h is y
+// rounded to 11 leading bits), so y = h + l to 2^-22 |y| (plus the FP16 subnormal spacing,
+// 2^-24, for the smallest values: below 2^-39 of the scale 2^15 the values are mapped to).
+// The pack conversion runs at the ALU rate on this part.
+__device__ inline uint32_t f16x2_pack(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
-// FP16 bits of v, which has at most 11 significant bits and |v| < 2^16; 0 below 2^-14.
-__device__ inline uint32_t f16_bits(float v) {
-  const uint32_t u = __float_as_uint(v), a = u & 0x7FFFFFFFu;
-  const uint32_t mag = a < 0x38800000u ? 0u : (a >> 13) - 0x1C000u;
-  return ((u >> 16) & 0x8000u) | mag;
+__device__ inline void f16_split2(float y0, float y1, uint32_t &h, uint32_t &l) {
+  h = f16x2_pack(y0, y1);
+  const float2 hv = __half22float2(*reinterpret_cast<const __half2 *>(&h));
+  l = f16x2_pack(__fsub_rn(y0, hv.x), __fsub_rn(y1, hv.y));
 }
-// y = h + l: the FP16 bits of both pieces.
-__device__ inline void f16_split(float y, uint32_t &h, uint32_t &l) {
-  const float hv = f16_lead(y);
-  h = f16_bits(hv);
-  l = f16_bits(f16_lead(__fsub_rn(y, hv)));
-}
-// FP32 value of FP16 bits written by f16_bits (normal or zero).
+// FP32 value of FP16 bits (normal, subnormal or zero).
 __host__ __device__ inline float f16_value(uint32_t h) {
-  const uint32_t a = h & 0x7FFFu;
-  const uint32_t u = ((h & 0x8000u) << 16) | (a ? (a << 13) + 0x38000000u : 0u);
 #ifdef __CUDA_ARCH__
-  return __uint_as_float(u);
+  return __half2float(__ushort_as_half((unsigned short)h));
 #else
-  float f;
-  __builtin_memcpy(&f, &u, 4);
-  return f;
+  const uint32_t e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
+  const float v = e ? std::ldexp((float)(1024u + m), (int)e - 25) : std::ldexp((float)m, -24);
+  return (h & 0x8000u) ? -v : v;
 #endif
 }
 }  // namespace pq

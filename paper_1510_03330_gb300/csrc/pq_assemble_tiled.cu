@@ -161,15 +161,9 @@ __device__ inline void put4(uint16_t *gam, uint16_t *fv, long long ps, long long
 
 // FP16 planes: the same four k' of Gamma X (scaled by sa) and F (scaled by sb) as h + l, planes
 // Gamma X (Re h, Re l, Im h, Im l) and F (Re h, Im h, Re l, Im l).
-__device__ inline uint2 pack4h(const uint32_t *v) { return make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16)); }
 __device__ inline void split4h(float sc, float x0, float x1, float x2, float x3, uint2 &h, uint2 &l) {
-  uint32_t hv[4], lv[4];
-  f16_split(sc * x0, hv[0], lv[0]);
-  f16_split(sc * x1, hv[1], lv[1]);
-  f16_split(sc * x2, hv[2], lv[2]);
-  f16_split(sc * x3, hv[3], lv[3]);
-  h = pack4h(hv);
-  l = pack4h(lv);
+  f16_split2(sc * x0, sc * x1, h.x, l.x);
+  f16_split2(sc * x2, sc * x3, h.y, l.y);
 }
 __device__ inline void put4h(uint16_t *gam, uint16_t *fv, long long ps, long long o, const float2 *gx,
                              const float2 *f, float sa, float sb) {

@@ -191,6 +191,8 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
     if (c->b.vfmt != ctxs[0]->b.vfmt)
       return bfail(nullptr, PQ_EINVAL, "member %d has another operand format than member 0", i);
     if (c->b.q_chunk < c->g.nk) return bfail(nullptr, PQ_EINVAL, "member %d runs in several passes", i);
+    if (c->opt.target_density > 0.0)
+      return bfail(nullptr, PQ_EINVAL, "member %d holds a fixed density (its mu search waits on the host)", i);
     if (c->st != ctxs[0]->st) return bfail(nullptr, PQ_EINVAL, "member %d uses another stream", i);
   }
   pq_batch *b = new pq_batch();

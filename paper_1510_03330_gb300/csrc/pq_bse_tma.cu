@@ -20,11 +20,13 @@
 //
 // Accumulation in chunks: the tensor cores add each MMA's products into the FP32
 // accumulator with a truncating alignment, so the error of a long accumulation grows
-// with the number of updates (about 1e-6 relative after the 384 updates of n = 1024).
-// The MMAs of one tile therefore accumulate KCH stages (KCH * 32 k) at a time into one
-// of the two tensor-memory accumulators, and the epilogue warps add each finished
-// chunk into FP32 registers (rounding to nearest) and release the accumulator for the
-// next chunk: the error per element is bounded by the chunk length, not by n.
+// with the number of updates (1.2e-6 relative on F_t after the 384 updates of n = 1024).
+// The MMAs of one tile therefore accumulate KCH stages (512 k) at a time into one of the
+// two tensor-memory accumulators, and the epilogue warps add each finished chunk into
+// FP32 registers (rounding to nearest) and release the accumulator for the next chunk:
+// the error per element is bounded by the chunk length, not by n.  Each epilogue thread
+// holds 64 such sums (one row, 32 complex columns), so 128-column tiles take 16 epilogue
+// warps and 64-column tiles 8.
 //
 // Operand layouts in shared memory (written by TMA, read by the MMAs):
 //   A plane: 128 rows x 32 k, K-major, 64-byte rows with the 64-byte swizzle;
@@ -57,7 +59,7 @@ constexpr int A_PLANE = BM * BK * 2;               // 8 KB
 constexpr int B_ATOM = BK * 128;                   // 4 KB: 32 k-rows x 64 columns
 constexpr int STAGE_A = 4 * A_PLANE;               // Arh Arl Aih Ail
 constexpr uint64_t WAIT_NS = 2000000000ull;        // 2 s per wait
-constexpr int KCH = 8;                             // stages (of BK k) per accumulator chunk
+constexpr int KCH = 16;                            // stages (of BK k) per accumulator chunk: 512 k
 
 // Tile geometry of the two variants: BNC complex output columns per tile.
 template <int BNC>

@@ -3,6 +3,7 @@
 // (Eq. PA_F_Phi), the second-order self-energy Sigma~1 in imaginary time
 // (Sec. II.B), the assembly and mixing of Sigma, and the susceptibility.
 // All arithmetic here is FP64.
+#include <algorithm>
 #include <cstdio>
 
 #include <cuda_bf16.h>
@@ -150,6 +151,45 @@ __global__ void split_scales_kernel(float *fsc, Bound4 lam_max) {
     u[FSC_PHIMAX + r] = 0u;
   }
   u[FSC_XMAX] = u[FSC_XMAX + 1] = 0u;
+}
+
+// Density per site (both spins) of G = [i nu + mu - eps_k - Sigma]^-1 on the square lattice, and
+// its derivative in mu: n = (2/N) sum_k [1/2 - beta c2/4 + T sum_nu Re(G - 1/(i nu) - c2/(i nu)^2)]
+// with c2 = eps_k - mu, the tails summed in closed form and the rest over n in [-M, M-1];
+// dn/dmu = (2/N) sum_k [beta/4 + T sum_nu Re(-G^2 + 1/(i nu)^2)] (dG/dmu = -G^2).  Partial sums
+// per block are added into out[0], out[1] (FP64 throughout).
+__global__ void density_kernel(Grid g, int M, const double2 *__restrict__ sigma, const double *__restrict__ c1p,
+                               double *__restrict__ out) {
+  __shared__ double r0[256], r1[256];
+  const long long total = (long long)g.nk * 2 * M;
+  double a = 0.0, b = 0.0;
+  const double c1 = c1p[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ik = (int)(i / (2 * M)), n = (int)(i % (2 * M)) - M;
+    const double nu = nu_of(g, n);
+    const double2 s = sigma_at(g, sigma, c1, ik, n);
+    const double2 gi = g0_inverse(g, ik, n) - s;  // i nu + mu - eps - Sigma
+    const double2 G = cinv(gi);
+    const double c2 = -(g0_inverse(g, ik, n).x);  // eps - mu
+    // Re(1/(i nu)) = 0, Re(c2/(i nu)^2) = -c2/nu^2; Re(1/(i nu)^2) = -1/nu^2
+    a += G.x + c2 / (nu * nu);
+    b += -(G.x * G.x - G.y * G.y) - 1.0 / (nu * nu);
+  }
+  r0[threadIdx.x] = a;
+  r1[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r0[threadIdx.x] += r0[threadIdx.x + w];
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&out[0], r0[0]);
+    atomicAdd(&out[1], r1[0]);
+  }
 }
 
 // Tail moments of G = 1/(i nu) + c2/(i nu)^2 + c3/(i nu)^3 + O(nu^-4).
@@ -406,6 +446,15 @@ cudaError_t launch_tail_and_green(cudaStream_t st, const Grid &g, Buffers &b) {
 cudaError_t launch_bubbles(cudaStream_t st, const Grid &g, Buffers &b) {
   unsigned *xmax = b.vfmt == V_F16P ? (unsigned *)(b.fsc + FSC_XMAX) : nullptr;
   bubbles_kernel<<<nblk((long long)g.nQ * g.n, 256), 256, 0, st>>>(g, b.gtab, b.xph, b.xpp, b.xph32, b.xpp32, xmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density(cudaStream_t st, const Grid &g, int M, const double2 *sigma, const double *c1,
+                           double *out2) {
+  cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)g.nk * 2 * M;
+  density_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, st>>>(g, M, sigma, c1, out2);
   return cudaGetLastError();
 }
 

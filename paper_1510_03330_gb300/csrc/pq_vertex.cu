@@ -151,7 +151,7 @@ __device__ inline uint32_t pack_pair(float x0, float x1) {
 // BF16 planes: x = h + l (+ r for F), each piece the BF16 rounding of what the previous
 // pieces leave (the differences are exact in FP32).  Plane order: Gamma X (Re h, Re l,
 // Im h, Im l), F (Re h, Im h, Re l, Im l, Re r, Im r).  FP16 planes: the channel's scaled
-// value x * 2^e = h + l (f16_split), planes Gamma X (Re h, Re l, Im h, Im l), F (Re h, Im h,
+// value x * 2^e = h + l (f16_split2), planes Gamma X (Re h, Re l, Im h, Im l), F (Re h, Im h,
 // Re l, Im l).
 template <typename S, int PL>
 struct Out {
@@ -172,15 +172,13 @@ struct Out {
       const float g0 = odd ? ga_in : ga.x, g1 = odd ? ga.y : ga_in;
       const float f0 = odd ? f_in : f.x, f1 = odd ? f.y : f_in;
       const int part = odd ? 1 : 0;
-      uint32_t h0, l0, h1, l1;
-      f16_split(sa * g0, h0, l0);
-      f16_split(sa * g1, h1, l1);
-      pg[(2 * part) * ps2 + o2] = h0 | (h1 << 16);
-      pg[(2 * part + 1) * ps2 + o2] = l0 | (l1 << 16);
-      f16_split(sb * f0, h0, l0);
-      f16_split(sb * f1, h1, l1);
-      pf[part * ps2 + o2] = h0 | (h1 << 16);
-      pf[(2 + part) * ps2 + o2] = l0 | (l1 << 16);
+      uint32_t h, l;
+      f16_split2(sa * g0, sa * g1, h, l);
+      pg[(2 * part) * ps2 + o2] = h;
+      pg[(2 * part + 1) * ps2 + o2] = l;
+      f16_split2(sb * f0, sb * f1, h, l);
+      pf[part * ps2 + o2] = h;
+      pf[(2 + part) * ps2 + o2] = l;
     } else if constexpr (PL == V_BF16P) {
       uint32_t *pg = (uint32_t *)gam, *pf = (uint32_t *)fv;
       const long long ps2 = ps >> 1;

@@ -49,6 +49,8 @@ class Params:
               the other leg; "lower": the lower edge alone (Sec. II.A).
     sde       "regulated": Sigma = Sigma~1 + Sigma~2 + the box sum of F - F~ (Sec. II.B);
               "truncated": Eq. PA_Sigma on the box with the vertex cut off there.
+    density   0: mu is fixed; > 0 (square lattice): electrons per site (both spins) to hold,
+              mu being searched at the start of every iteration on the state's Sigma.
     """
 
     lattice: str
@@ -67,6 +69,7 @@ class Params:
     kernel_level: int = 2
     edge_rule: str = "both"
     sde: str = "regulated"
+    density: float = 0.0
 
     @property
     def n_k(self) -> int:
@@ -101,6 +104,9 @@ CONFIGS = {
     # the large solve's frequency box on the 4x4 lattice (n = 384, 0.45 GB of Phi): a small
     # case of the same kernels for profiling captures
     "square4_u3_b8_nu24": Params(SQUARE, beta=8.0, U=3.0, mu=0.0, L=4, n_nu=24, n_Omega=24),
+    # BSE matrices of the 8x8 workload's size (n = 1024) on 64 transfer slices (4x4 momenta,
+    # Nnu = 64, NOmega = 1; 0.5 GB of Phi): the n = 1024 products for profiling captures
+    "square4_nu64_om1": Params(SQUARE, beta=4.0, U=2.0, mu=0.0, L=4, n_nu=64, n_Omega=1),
 }
 
 

@@ -61,10 +61,13 @@ def test_batch_members_follow_their_own_iteration(tile_cols, order, precision):
         assert all(x > 0 for x in cfg["tuned_ms"]), cfg
     assert t["bse"] > 0 and t["iteration"] >= t["bse"]
     assert np.all(np.isfinite(d)) and np.all(d > 0)
+    # the grouped launch may use another tile width than the members alone (another order of
+    # the FP32 sums), so the two agree to the format's accuracy, not to the bit
+    tol, tol_phi = PLANE[precision]
     for p, a, m in zip(MEMBERS, alone, mem):
-        assert rel(m.sigma(), a.sigma()) < 1e-6, p
-        assert rel(all_phi(m, p), all_phi(a, p)) < 1e-6, p
-        assert rel(m.chi(1), a.chi(1)) < 1e-6, p
+        assert rel(m.sigma(), a.sigma()) < tol, p
+        assert rel(all_phi(m, p), all_phi(a, p)) < tol_phi, p
+        assert rel(m.chi(1), a.chi(1)) < tol, p
     for s in alone + mem:
         s.close()
 

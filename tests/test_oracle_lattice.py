@@ -275,3 +275,43 @@ def test_particle_hole_symmetry_4x4():
     assert np.abs(s[swp] - s).max() < 1e-13 * scale
     # the momentum dependence is real: Sigma differs between k = 0 and k = (pi, pi)
     assert np.abs(s[0] - s[idx(p, 2, 2)]).max() > 1e-3 * scale
+
+
+# --------------------------------------------------------------------------- density and mu search
+
+
+@pytest.mark.parametrize("L,mu", [(3, 0.35), (4, -0.8), (4, 0.0)])
+def test_density_of_the_free_lattice_is_the_fermi_sum(flux, L, mu):
+    """With Sigma = 0 the density is (2/N) sum_k f(eps_k - mu), the flux lattice included:
+    checks the closed-form tails (1/2 and -beta c2/4) and the remainder sum."""
+    p = Params("square", beta=3.0, U=1.0, mu=mu, L=L, n_nu=4, n_Omega=3, hop=0.9)
+    n = O.density(p, np.zeros((L * L, p.n_ext), complex))
+    e = np.array([flux_eps(p, *coords(p, i)) for i in range(L * L)])
+    ref = 2.0 * np.mean(fermi(e - mu, p.beta))
+    assert abs(n - ref) < 1e-9, (n, ref)
+
+
+def test_density_is_monotone_and_half_filled_at_mu_zero():
+    """At half filling of the plain lattice (mu = 0, particle-hole symmetric Sigma after three
+    iterations) n = 1; n(mu) increases with mu at fixed Sigma; find_mu inverts it."""
+    p = Params("square", beta=2.0, U=1.4, mu=0.0, L=4, n_nu=4, n_Omega=3)
+    sig = iterated(p, 3).state.sigma
+    assert abs(O.density(p, sig) - 1.0) < 1e-12
+    ns = [O.density(p.with_(mu=m), sig) for m in (-1.0, -0.3, 0.2, 0.9)]
+    assert all(b > a for a, b in zip(ns, ns[1:])), ns
+    for target in (0.8, 1.15):
+        mu = O.find_mu(p, sig, target)
+        assert abs(O.density(p.with_(mu=mu), sig) - target) < 1e-11
+
+
+def test_fixed_density_iteration_holds_the_density():
+    """An iteration at fixed density (p.density) sets mu on the state's Sigma before the
+    Dyson step: the G of that iteration holds the target filling; away from half filling
+    the second-order self-energy acquires a real part."""
+    p = Params("square", beta=2.5, U=1.2, mu=0.0, L=3, n_nu=4, n_Omega=3, density=0.85)
+    st = O.zero_state(p)
+    for _ in range(2):
+        res = O.iterate(p, st)
+        assert abs(O.density(p.with_(mu=res.mu, density=0.0), st.sigma) - 0.85) < 1e-11
+        st = res.state
+    assert res.mu < 0 and np.abs(st.sigma.real).max() > 1e-4

@@ -17,6 +17,11 @@ from paper_1510_03330_gb300.workloads import Params, random_state
 TOL_FP64 = 1e-10
 P = Params("square", beta=2.5, U=1.3, mu=0.1, L=2, n_nu=8, n_Omega=7, hop=0.9,
            tau_matsubara=256, tau_panels=16, tau_order=16)
+# every region of the static scratch at its maximum: L * L = 16 momenta (complex phases
+# exp(i k.r), where a conjugation slip would show), 2 * tau_matsubara = 512,
+# tau_panels * tau_order = 512 nodes, NOmega + Nnu - 1 = 128 frequencies
+P_MAX = Params("square", beta=3.0, U=1.1, mu=-0.2, L=4, n_nu=2, n_Omega=127, hop=0.8,
+               tau_matsubara=256, tau_panels=32, tau_order=16)
 
 
 def _call(lib, p, src, dst, stream):
@@ -26,7 +31,8 @@ def _call(lib, p, src, dst, stream):
 
 
 @pytest.mark.gpu
-def test_noalloc_matches_the_allocating_entry_point_on_two_calls():
+@pytest.mark.parametrize("P", [P, P_MAX], ids=["2x2", "4x4_max"])
+def test_noalloc_matches_the_allocating_entry_point_on_two_calls(P):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
