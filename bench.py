@@ -42,13 +42,14 @@ DTYPE = {FP64: "f64", SPLIT_TF32X3: "tf32x3 (split TF32 operands, fp32 accumulat
          SPLIT_FP16X3: "fp16x3 (split FP16 operands, power-of-two scaled per channel, fp32 accumulate in chunks)",
          SPLIT_BF16X6: "bf16x6"}
 PLANES = (SPLIT_BF16X3, SPLIT_FP16X3)
-# DRAM bytes of one launch / algorithmic bytes (ncu dram__bytes_read + dram__bytes_write).
-# Measured at full size by a one-pass capture of the launch itself for the workload and scheme
-# it was taken on (8x8 BF16x3: products 166.5 GB, assembly 146.2 GB); otherwise from a capture
-# of the TF32x3 products on the 4x4 lattice, scaled by the launch's size; kernels changed since
-# a capture have none.
+# DRAM bytes of one launch of the products / their algorithmic bytes (32 n^2 per GEMM), from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on a small
+# batch, scaled to the launch by its GEMM count (the traffic of one GEMM depends on n, not on the
+# batch): FP16x3 at n = 1024 on 64 GEMMs; TF32x3 at n = 256 on the 4x4 lattice, scaled by
+# n^2 x batch.  Kernels changed since a capture have none.
+BSE_TRAFFIC = {SPLIT_FP16X3: (1.047, "ncu capture of this kernel at n = 1024 on 64 GEMMs, scaled by the GEMM count"),
+               SPLIT_TF32X3: (0.986, "ncu capture on the 4x4 lattice scaled by n^2 x batch")}
 FULL_TRAFFIC = {}
-BSE_TRAFFIC = {SPLIT_TF32X3: 0.986}
 # kernels launched by one iteration: Dyson (2), bubbles (1), K1/K2 (1), Sigma~1 (7),
 # Sigma~2 (8: tables, their prefix sums, two output passes), parquet assembly (1),
 # Sigma update (1), BSE (1); FP16 planes add the kernel of the operand scales (1)
@@ -576,8 +577,8 @@ def main():
         # DRAM bytes per launch as a multiple of the algorithmic 32 n^2 bytes per GEMM (read A,
         # B, Phi; write Phi)
         tr, tsrc = full_tr.get("bse"), "ncu capture of this launch at full size"
-        if tr is None and a.precision in BSE_TRAFFIC:
-            tr, tsrc = BSE_TRAFFIC[a.precision], "ncu capture on the 4x4 lattice scaled by n^2 x batch"
+        if tr is None and a.precision in BSE_TRAFFIC and (a.precision != SPLIT_FP16X3 or n == 1024):
+            tr, tsrc = BSE_TRAFFIC[a.precision]
         bse_roof = {"bound": "tensor", "achieved": bse_tflops, "peak": peak, "unit": "TFLOP/s",
                     "frac": bse_tflops / peak, "traffic": tr * 32.0 * n * n * 4 * nQ if tr else None,
                     "traffic_source": tsrc if tr else None,

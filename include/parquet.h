@@ -54,7 +54,7 @@ typedef enum {
   PQ_ETIMEOUT = 5, /* a bounded device wait gave up; the context is poisoned */
   PQ_ENAN = 6,     /* a non-finite Sigma appeared; the context is poisoned */
   PQ_ESTATE = 7,   /* the context is poisoned by an earlier PQ_ECUDA/PQ_ENAN/PQ_ETIMEOUT */
-  PQ_EDIVERGED = 8 /* pq_iterate stopped: max |dSigma| grew diverge_window times in a row (state is valid) */
+  PQ_EDIVERGED = 8 /* pq_iterate stopped on divergence (pq_options.diverge_window); the state is valid */
 } pq_status;
 
 typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
@@ -122,8 +122,10 @@ typedef struct {
    * flop: slower on large matrices). */
   int bse_tile_cols;
   /* Divergence detection in pq_iterate: when max |dSigma| has grown in each of the last
-   * diverge_window iterations, stop with PQ_EDIVERGED (the iteration that diverges is kept:
-   * the state is valid, e.g. for a restart with stronger mixing).  0 (default): off. */
+   * diverge_window iterations and is more than 10 times the smallest max |dSigma| of the
+   * call (a damped iteration can rise for a while without running away), stop with
+   * PQ_EDIVERGED (the iteration that diverges is kept: the state is valid, e.g. for a
+   * restart with stronger mixing).  0 (default): off. */
   int diverge_window;
   /* Filling: 0 (default) keeps mu fixed; a value in (0, 2) (square lattice) is the number of
    * electrons per site (both spins) to hold: every iteration first sets mu, by a Newton search

@@ -6,8 +6,9 @@ U = 6 and 8 for beta = 2, with its quality degrading there (the large-U paragrap
 figure).  This module runs that scan on the GPU solver: for each U and each linear-mixing
 weight alpha it iterates the Bethe single-site solve from Phi = 0, Sigma = 0 until
 max|dSigma| < tol, until divergence is detected (max|dSigma| growing for `window` iterations
-in a row, pq_options.diverge_window) or until max_iter, and records the outcome, the
-iteration count, the last max|dSigma|, Im Sigma at the lowest Matsubara frequency, and the
+in a row to more than 10x its minimum, pq_options.diverge_window) or until max_iter, and
+records the outcome, the iteration count, the last max|dSigma|, Im Sigma at the lowest
+Matsubara frequency, and the
 high-frequency tail coefficient c1 = -nu Im Sigma(i nu) at the edge of the stored range,
 which the regulated self-energy keeps near U^2 n (1 - n) = U^2 / 4 (Sec. II.B).
 
@@ -89,7 +90,7 @@ def run_point(p: Params, runner, max_iter: int, tol: float, window: int) -> Stud
 
 
 def pa_convergence_study(Us=(1.0, 2.0, 4.0, 6.0, 8.0), alphas=(0.5, 0.3, 0.1), beta: float = 2.0,
-                         n_nu: int = 16, n_Omega: int = 15, max_iter: int = 300, tol: float = 1e-8,
+                         n_nu: int = 16, n_Omega: int = 15, max_iter: int = 1000, tol: float = 1e-8,
                          window: int = 8, runner=None) -> list[StudyPoint]:
     """The scan over U and alpha (see the module docstring)."""
     runner = runner or gpu_runner
@@ -112,7 +113,7 @@ def main(argv=None) -> int:
     ap.add_argument("--beta", type=float, default=2.0)
     ap.add_argument("--n-nu", type=int, default=16)
     ap.add_argument("--n-Omega", type=int, default=15)
-    ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--window", type=int, default=8)
     ap.add_argument("--json", default=None)
