@@ -319,7 +319,7 @@ def run_batch(a, world, barrier, clk_factory):
         wave_seq = e0.elapsed_time(e1)
         seq_ms += wave_seq
         b = Batch(sols, time_steps=True)
-        b.iterate(a.warmup + 4)  # the first iterations tune the grouped launch, then the graph is captured
+        b.iterate(a.warmup + 5)  # a warm-up and four tuning iterations, then the graph is captured
         torch.cuda.synchronize()
         barrier()
         f0, f1 = ev(), ev()

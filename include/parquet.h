@@ -122,8 +122,9 @@ typedef struct {
    * flop: slower on large matrices). */
   int bse_tile_cols;
   /* Divergence detection in pq_iterate: when max |dSigma| has grown in each of the last
-   * diverge_window iterations and is more than 10 times the smallest max |dSigma| of the
-   * call (a damped iteration can rise for a while without running away), stop with
+   * diverge_window iterations and is more than 10 times the largest max |dSigma| of the
+   * first diverge_window iterations of the call (a damped iteration oscillates, rising for
+   * a while without running away), stop with
    * PQ_EDIVERGED (the iteration that diverges is kept: the state is valid, e.g. for a
    * restart with stronger mixing).  0 (default): off. */
   int diverge_window;
@@ -284,10 +285,10 @@ typedef struct {
 /* Fill *opt with the defaults: tune both choices, no timing. */
 PQ_API void pq_batch_default_options(pq_batch_options *opt);
 
-/* Group count contexts.  When a choice is left to tuning, the first
- * iterations of pq_batch_iterate run the candidate grouped kernels in turn
- * (each a full, real iteration: the candidates compute the same products) and
- * keep the fastest; the graph is captured after that.  Errors: PQ_EINVAL (a
+/* Group count contexts.  When a choice is left to tuning, the first iteration
+ * of pq_batch_iterate runs untimed (warm-up) and the next ones run the candidate
+ * grouped kernels in turn (each a full, real iteration: the candidates compute
+ * the same products), keeping the fastest; the graph is captured after that.  Errors: PQ_EINVAL (a
  * member that does not qualify, count < 1), PQ_ENOMEM, PQ_ECUDA;
  * pq_last_error(NULL) gives the message. */
 PQ_API pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const pq_batch_options *opt);

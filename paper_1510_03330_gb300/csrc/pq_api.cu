@@ -22,7 +22,7 @@ using pq::Sizes;
 namespace {
 
 std::string g_init_err;
-constexpr double kDivergeFactor = 10.0;  // divergence detection: growth over the minimum max |dSigma|
+constexpr double kDivergeFactor = 10.0;  // divergence detection: growth over the first max |dSigma|
 
 const char *kStepNames[PQ_NSTEPS] = {"dyson",    "bubbles",      "kernels", "sigma1", "sigma2",
                                      "assemble", "sigma_update", "bse",     "total"};
@@ -681,7 +681,7 @@ pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, doubl
   if (c->poisoned) return fail(c, PQ_ESTATE, "context poisoned by an earlier error: %s", c->err.c_str());
   if (max_iter < 0) return fail(c, PQ_EINVAL, "max_iter < 0");
   if (c->in_batch) return fail(c, PQ_EINVAL, "the context belongs to a batch: iterate it with pq_batch_iterate");
-  double d = INFINITY, prev = INFINITY, dmin = INFINITY;
+  double d = INFINITY, prev = INFINITY, dref = 0.0;
   int it = 0, grown = 0;
   const int win = c->opt.diverge_window;
   for (; it < max_iter; ++it) {
@@ -696,14 +696,14 @@ pq_status pq_iterate(pq_ctx *c, int max_iter, double tol, int *iters_done, doubl
     }
     grown = d > prev ? grown + 1 : 0;  // consecutive iterations whose max |dSigma| grew
     prev = d;
-    dmin = std::min(dmin, d);
-    // diverging: grown win times in a row and 10x above the smallest change of this call (a
-    // damped iteration can rise for a while without running away)
-    if (win > 0 && grown >= win && d > kDivergeFactor * dmin) {
+    if (it < win) dref = std::max(dref, d);  // the changes of the first win iterations of the call
+    // diverging: grown win times in a row and 10x above the first changes of this call (a
+    // damped iteration oscillates, rising for a while without running away)
+    if (win > 0 && grown >= win && d > kDivergeFactor * dref) {
       if (iters_done) *iters_done = it + 1;
       if (last) *last = d;
-      return fail(c, PQ_EDIVERGED, "max |dSigma| grew in each of the last %d iterations to %.3e (%.0fx its minimum)",
-                  win, d, d / dmin);
+      return fail(c, PQ_EDIVERGED, "max |dSigma| grew in each of the last %d iterations to %.3e (%.0fx its first values)",
+                  win, d, d / dref);
     }
   }
   if (iters_done) *iters_done = it;

@@ -32,6 +32,24 @@ __device__ inline C lam_at(const Lam &lam, int r, C l_r, int m, int n, int np_) 
   return l_r;
 }
 
+// Running complex sum in FP32 with its rounding error kept (Knuth's TwoSum on each part):
+// s + c holds the sum of the terms added to about twice FP32 precision, which for FP32 terms
+// is as accurate as an FP64 accumulator, without FP64 work per term (the FP64 pipe is narrow
+// on this part).  The split assemblies add each step's partial dF sum into one.
+struct CSum2 {
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+  __device__ static inline void two_sum(float &s, float &c, float x) {
+    const float t = s + x, z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ inline void add(float2 v) {
+    two_sum(sx, cx, v.x);
+    two_sum(sy, cy, v.y);
+  }
+  __device__ inline double2 get() const { return make_double2((double)sx + (double)cx, (double)sy + (double)cy); }
+};
+
 // BF16 rounding (to nearest, ties to even) of finite FP32 values in integer arithmetic:
 // the upper half of u + 0x7FFF + (bit 16 of u).  Identical to the hardware conversion,
 // but it runs on the integer ALU instead of the conversion unit, which is narrow on this

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(TT, 2)
 
   const float2 l0 = f2(lam.l[0]), l1 = f2(lam.l[1]), l2 = f2(lam.l[2]), l3 = f2(lam.l[3]);
   const float2 twoU = make_float2((float)(2.0 * g.U), 0.f);
-  float2 acc = make_float2(0.f, 0.f);
+  CSum2 acc;  // this thread's dF box sum: a compensated sum of the per-step partial sums
   Ctx c{Rt, Pt, St, FK, G, t.RS, t.RA, t.PW, t.BW, nom, nnu, a, 4 * (cu % t.hb), n, row0};
   // this thread's delay line: a slots of 8 float4 (Gamma X_s, Gamma X_t, F_s, F_t of 4 elements)
   float4 *dl = ring + (size_t)8 * t.ring_n * (a * (a - 1) / 2) + row0 * t.hb + cu % t.hb;
@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(TT, 2)
     if (tid < G && step + 1 < nsteps)
       step_table(g, step_dm(step + 1), step_q(step + 1), ik, p0, tid, stab[(step + 1) & 1] + tid * T_N);
 
+    float2 sacc = make_float2(0.f, 0.f);  // this step's part of the dF box sum
     for (int mi = row0; worker && mi < nom; mi += t.rows) {
       c.mi = mi;
       const int m = g.m_lo + mi;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(TT, 2)
         float2 xq[4];
         load4(xph + (long long)Q * nn + col0, xq);
         const float2 gkq = gtab[(long long)tb[T_CM] * g.n_g + (n + m - g.g_lo)];
-        elems_dm<TAB>(g, c, lam, l0, l1, twoU, xq, gkq, gx, f, acc);
+        elems_dm<TAB>(g, c, lam, l0, l1, twoU, xq, gkq, gx, f, sacc);
         const long long o = ((long long)(Q - pass.qb * nom) * nn + k) * ld + col0;
         put_ops<PF>(gam, fv, ps, o, gx[0], f[0], ssc, 0);
         put_ops<PF>(gam, fv, ps, ochan + o, gx[1], f[1], ssc, 1);
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(TT, 2)
         float2 xqp[4];
         load4(xpp + (long long)Qp * nn + col0, xqp);
         const float2 gqk = gtab[(long long)tb[a * T_N + T_PQK] * g.n_g + (m - n - 1 - g.g_lo)];
-        elems_st<TAB>(g, c, lam, l2, l3, twoU, xqp, gqk, gx, f, acc);
+        elems_st<TAB>(g, c, lam, l2, l3, twoU, xqp, gqk, gx, f, sacc);
         if constexpr (FUSED) {
           // Block 0 of row q0 = k + p_0 + q is produced now; block a >= 1 of that row was
           // produced a steps ago (same lattice row of q) and waits in the delay line.  All
@@ -437,11 +438,12 @@ __global__ void __launch_bounds__(TT, 2)
         }
       }
     }
+    acc.add(sacc);
     __syncthreads();  // the tiles are free for the next gather
   }
 
   // dF box sum per (k, p_a): the threads of block a
-  red[tid] = make_double2(acc.x, acc.y);
+  red[tid] = acc.get();
   __syncthreads();
   if (tid < G) {
     double2 s = make_double2(0.0, 0.0);

@@ -6,8 +6,9 @@
 // first tile of each, so small and large solves share the SMs in one schedule.
 // The whole iteration (members' steps, grouped products, gather of the members'
 // convergence scalars and their device->host copy) is captured once as a CUDA
-// graph and replayed; the members' steps are captured on four branch streams
-// (round robin), so the graph runs independent members concurrently.  Two choices of the grouped launch are tuned on the first
+// graph and replayed; the members' steps are captured on four branch streams (the members
+// with n >= 512 one after another on the first, the smaller ones round robin on the other
+// three), so the graph runs independent small members concurrently.  Two choices of the grouped launch are tuned on the first
 // real iterations: the tile width (64 or 128 complex output columns; narrow tiles
 // waste less of the MMA on small matrices) and the order of the members in the
 // schedule (as given, or largest matrix first so the longest tiles start early).
@@ -34,6 +35,8 @@ struct pq_batch {
   double *host = nullptr;          // pinned copy of gather
   int *err = nullptr;              // device: timeout flag of the grouped kernel
   std::vector<std::pair<int, int>> cand;  // candidate (tile index, order) still to time
+  bool warmed = false;             // the untimed first iteration that precedes the tuning ran
+  std::vector<int> branch;         // branch stream of each member
   float tuned[4] = {0, 0, 0, 0};
   int tile = -1, order = -1;       // chosen (indices into tab)
   cudaGraph_t graph = nullptr;
@@ -102,7 +105,7 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph
   for (size_t i = 0; i < b->m.size(); ++i) {
     pq_ctx *c = b->m[i];
     cudaStream_t keep = c->st;
-    c->st = b->br[i % nbr];
+    c->st = b->br[b->branch[i] % nbr];
     pq_status s = pq::enqueue_iteration(c, false, false);
     c->st = keep;
     if (s != PQ_OK) return bfail(b, s, "member step failed: %s", c->err.c_str());
@@ -257,6 +260,13 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
     b->order = b->cand[0].second;
     b->cand.clear();
   }
+  // branch streams: the members whose matrices fill the GPU (n >= 512) run their steps one
+  // after another on branch 0, where concurrency would only contend for it; the smaller ones
+  // are spread over the other branches, so their short kernels overlap
+  b->branch.assign(count, 0);
+  int next = 0;
+  for (int i = 0; i < count; ++i)
+    if (ctxs[i]->g.n < 512) b->branch[i] = 1 + (next++ % 3);
   for (pq_ctx *c : b->m) c->in_batch = true;
   *out = b;
   return PQ_OK;
@@ -269,7 +279,15 @@ pq_status pq_batch_iterate(pq_batch *b, int n_iter, double *max_dsigma) {
   BCK(cudaStreamSynchronize(b->user_st));
   const int n = (int)b->m.size();
   for (int it = 0; it < n_iter; ++it) {
-    if (!b->cand.empty()) {
+    if (!b->cand.empty() && !b->warmed) {
+      // the first iteration runs untimed with the first candidate: the candidates are then
+      // timed on equal terms (clocks up, caches and the members' tables warm)
+      const auto cnd = b->cand.front();
+      pq_status s = enqueue_all(b, cnd.first, cnd.second, false);
+      if (s != PQ_OK) return s;
+      BCK(cudaStreamSynchronize(b->st));
+      b->warmed = true;
+    } else if (!b->cand.empty()) {
       // tuning: this iteration runs the next candidate, eagerly, with its grouped launch timed
       const auto cnd = b->cand.front();
       pq_status s = enqueue_all(b, cnd.first, cnd.second, true);

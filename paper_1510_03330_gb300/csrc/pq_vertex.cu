@@ -130,6 +130,24 @@ template <typename C> __device__ inline double2 cdbl(C v);
 template <> __device__ inline double2 cdbl<double2>(double2 v) { return v; }
 template <> __device__ inline double2 cdbl<float2>(float2 v) { return make_double2(v.x, v.y); }
 
+// The dF box sum of a thread across the gather steps: in FP64 the accumulator itself; in the
+// FP32 (split) paths each step's partial sum is moved into a compensated sum (CSum2), so the
+// sum over all transfers keeps FP64-grade accuracy.
+template <typename C>
+struct DfSum {
+  __device__ inline void step(C &) {}
+  __device__ inline double2 get(const C &acc) const { return cdbl<C>(acc); }
+};
+template <>
+struct DfSum<float2> {
+  CSum2 s;
+  __device__ inline void step(float2 &acc) {
+    s.add(acc);
+    acc = make_float2(0.f, 0.f);
+  }
+  __device__ inline double2 get(const float2 &) const { return s.get(); }
+};
+
 // (k', k'+1) values -> packed BF16 pair (k' in the low half) and the FP32 remainders
 __device__ inline uint32_t split_pair(float x0, float x1, float &r0, float &r1) {
   const uint32_t a = bf16_round(x0), b = bf16_round(x1);
@@ -257,7 +275,8 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
   const C l0 = cfrom<C>(lam.l[0]), l1 = cfrom<C>(lam.l[1]), l2 = cfrom<C>(lam.l[2]), l3 = cfrom<C>(lam.l[3]);
   const double2 U2 = make_double2(2.0 * g.U, 0.0);
   const C twoU = cfrom<C>(U2);
-  C acc = cz<C>();
+  C acc = cz<C>();     // FP64 path: the dF box sum itself
+  DfSum<C> acc_all;    // split paths: a compensated sum of the per-step partial sums
 
   const int nstep = pass.fused ? 1 : 2;
   for (int iqc = pass.qb; iqc < pass.qb + pass.nq; ++iqc)
@@ -282,6 +301,7 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
       St[e] = phi[3 * chan + srow];
     }
     __syncthreads();
+    acc_all.step(acc);
     for (int e = threadIdx.x; e < NB; e += blockDim.x) {
       const int mi = (int)__umulhi((unsigned)e, nnu_magic), npi = e - mi * g.n_nu;
       const int m = g.m_lo + mi, np_ = g.n_lo + npi;
@@ -354,7 +374,8 @@ __global__ void __launch_bounds__(256, 4) assemble_kernel(Grid g, const S *__res
       }
     }
   }
-  red[threadIdx.x] = cdbl<C>(acc);
+  acc_all.step(acc);
+  red[threadIdx.x] = acc_all.get(acc);
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];

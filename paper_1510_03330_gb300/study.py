@@ -6,7 +6,7 @@ U = 6 and 8 for beta = 2, with its quality degrading there (the large-U paragrap
 figure).  This module runs that scan on the GPU solver: for each U and each linear-mixing
 weight alpha it iterates the Bethe single-site solve from Phi = 0, Sigma = 0 until
 max|dSigma| < tol, until divergence is detected (max|dSigma| growing for `window` iterations
-in a row to more than 10x its minimum, pq_options.diverge_window) or until max_iter, and
+in a row to 10x its first values, pq_options.diverge_window) or until max_iter, and
 records the outcome, the iteration count, the last max|dSigma|, Im Sigma at the lowest
 Matsubara frequency, and the
 high-frequency tail coefficient c1 = -nu Im Sigma(i nu) at the edge of the stored range,

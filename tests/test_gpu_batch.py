@@ -44,7 +44,7 @@ def all_phi(s, p):
 def test_batch_members_follow_their_own_iteration(tile_cols, order, precision):
     from paper_1510_03330_gb300.binding import Batch, Solver
 
-    iters = 6  # with tuning: four candidate iterations, then the captured graph
+    iters = 7  # with tuning: a warm-up and four candidate iterations, then the captured graph
     alone = [Solver(p, precision=precision) for p in MEMBERS]
     for s in alone:
         s.iterate(iters)
