@@ -304,16 +304,19 @@ def run_batch(a, world, barrier, clk_factory):
     clk = clk_factory()
     clk.start()
     for w in waves:
-        sols = [Solver(draw[i], precision=prec, q_chunk=draw[i].n_k) for i in w]
+        sols = [Solver(draw[i], precision=prec, q_chunk=draw[i].n_k, time_steps=True) for i in w]
         for s_ in sols:
             s_.iterate(1)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = ev(), ev()
         e0.record(stream)
+        seq_steps = {}
         for _ in range(a.steps):
             for s_ in sols:
                 s_.iterate(1)
+                for k_, v_ in s_.step_times().items():  # each iteration ends synchronised
+                    seq_steps[k_] = seq_steps.get(k_, 0.0) + v_
         e1.record(stream)
         torch.cuda.synchronize()
         wave_seq = e0.elapsed_time(e1)
@@ -324,10 +327,11 @@ def run_batch(a, world, barrier, clk_factory):
         barrier()
         f0, f1 = ev(), ev()
         f0.record(stream)
-        bse = 0.0
+        bse = it_ms = 0.0
         for _ in range(a.steps):
             b.iterate(1)
             bse += b.times()["bse"]
+            it_ms += b.times()["iteration"]
         f1.record(stream)
         torch.cuda.synchronize()
         wave_bat = f0.elapsed_time(f1)
@@ -335,7 +339,10 @@ def run_batch(a, world, barrier, clk_factory):
         bse_ms += bse
         tuned.append(dict(b.config(), solves=len(w), max_n=max(draw[i].n for i in w),
                           one_at_a_time_ms=wave_seq / a.steps, batched_ms=wave_bat / a.steps,
-                          batched_over_one_at_a_time=wave_seq / wave_bat))
+                          batched_over_one_at_a_time=wave_seq / wave_bat,
+                          one_at_a_time_bse_ms=seq_steps.get("bse", 0.0) / a.steps,
+                          one_at_a_time_assemble_ms=seq_steps.get("assemble", 0.0) / a.steps,
+                          batched_bse_ms=bse / a.steps, batched_members_ms=(it_ms - bse) / a.steps))
         b.close()
         for s_ in sols:
             s_.close()

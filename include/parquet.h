@@ -62,8 +62,12 @@ typedef enum { PQ_BETHE = 0, PQ_SQUARE = 1 } pq_lattice;
 /* Arithmetic of the vertex storage and the BSE products.
  * PQ_FP64: complex128 vertices, FP64 everywhere.
  * PQ_SPLIT_*: complex64 Phi, parquet assembly in FP32; the BSE runs on the
- * tensor cores as a split-operand product with FP32 accumulation; Dyson,
- * K1/K2 and the Sigma sums stay FP64.
+ * tensor cores as a split-operand product with FP32 accumulation; Dyson, the
+ * bubbles, Sigma~1 and Sigma~2 stay FP64.  The parts of Sigma and K1/K2 that
+ * read the FP32 vertex are sums of FP32 products kept as compensated FP32
+ * (two-sum) accumulators and reduced in FP64: the dF box sum of Eq. PA_Sigma
+ * (per assembly thread, one FP32 partial per gather step added into the
+ * compensated sum) and the edge sums of K1/K2 (Sec. II.A).
  *   PQ_SPLIT_TF32X3: complex64 operands split into TF32 hi/lo inside the GEMM
  *     (~2^-22 per product);
  *   PQ_SPLIT_BF16X3: the assembly writes the operands as BF16 planes (hi/lo;

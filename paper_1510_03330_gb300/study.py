@@ -12,7 +12,7 @@ Matsubara frequency, and the
 high-frequency tail coefficient c1 = -nu Im Sigma(i nu) at the edge of the stored range,
 which the regulated self-energy keeps near U^2 n (1 - n) = U^2 / 4 (Sec. II.B).
 
-    python -m paper_1510_03330_gb300.study [--U 1 2 4 6 8] [--alpha 0.5 0.3 0.1] [--json out.json]
+    python -m paper_1510_03330_gb300.study [--U 1 2 4 6 8] [--alpha 0.5 0.3 0.1 0.05] [--json out.json]
 
 The iteration itself runs in the CUDA library; this module only drives it and tabulates.
 A runner other than the GPU one can be passed (same call signature) to drive another
@@ -89,8 +89,8 @@ def run_point(p: Params, runner, max_iter: int, tol: float, window: int) -> Stud
                       tail_ref=p.U**2 / 4.0, seconds=secs)
 
 
-def pa_convergence_study(Us=(1.0, 2.0, 4.0, 6.0, 8.0), alphas=(0.5, 0.3, 0.1), beta: float = 2.0,
-                         n_nu: int = 16, n_Omega: int = 15, max_iter: int = 1000, tol: float = 1e-8,
+def pa_convergence_study(Us=(1.0, 2.0, 4.0, 6.0, 8.0), alphas=(0.5, 0.3, 0.1, 0.05), beta: float = 2.0,
+                         n_nu: int = 16, n_Omega: int = 15, max_iter: int = 3000, tol: float = 1e-8,
                          window: int = 8, runner=None) -> list[StudyPoint]:
     """The scan over U and alpha (see the module docstring)."""
     runner = runner or gpu_runner
@@ -109,11 +109,11 @@ def format_table(points: list[StudyPoint]) -> str:
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--U", type=float, nargs="+", default=[1.0, 2.0, 4.0, 6.0, 8.0])
-    ap.add_argument("--alpha", type=float, nargs="+", default=[0.5, 0.3, 0.1])
+    ap.add_argument("--alpha", type=float, nargs="+", default=[0.5, 0.3, 0.1, 0.05])
     ap.add_argument("--beta", type=float, default=2.0)
     ap.add_argument("--n-nu", type=int, default=16)
     ap.add_argument("--n-Omega", type=int, default=15)
-    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--window", type=int, default=8)
     ap.add_argument("--json", default=None)
