@@ -264,8 +264,11 @@ PQ_API pq_status pq_sigma_second_order_noalloc(int lattice, double beta, double 
  * A batch iterates several independent solves of uneven size together on one
  * GPU.  Each iteration is one CUDA graph launch: every member's one-particle,
  * kernel-function, self-energy and assembly steps, then ONE persistent grouped
- * kernel over the tiles of all members' Bethe-Salpeter products, then a gather
- * of every member's convergence scalars for a single device->host read.
+ * kernel over the tiles of the Bethe-Salpeter products of the members with
+ * n < 512, then a gather of every member's convergence scalars for a single
+ * device->host read.  A member with n >= 512 (its products fill the GPU alone)
+ * runs its products in its own launch right after its other steps, as it does
+ * outside a batch.
  * Members: contexts made by pq_init with PQ_SPLIT_BF16X3, or all with
  * PQ_SPLIT_FP16X3, and a single pass (q_chunk 0 or >= L*L, and the box fits),
  * on one device and one cuda_stream,
@@ -304,13 +307,15 @@ PQ_API pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count,
 PQ_API pq_status pq_batch_iterate(pq_batch *b, int n_iter, double *max_dsigma);
 
 /* The grouped kernel's configuration: tile columns, order (as in
- * pq_batch_options; -1 while tuning is not finished) and, when tuned, the
+ * pq_batch_options; -1 while tuning is not finished, and when no member has
+ * n < 512, so that there is no grouped kernel) and, when tuned, the
  * device time in ms of each candidate (tile_cols 128/64 x order 0/1, in that
  * order; 0 where not run) in tuned_ms[4]. */
 PQ_API pq_status pq_batch_config(const pq_batch *b, int *tile_cols, int *order, float *tuned_ms);
 
 /* Device times (ms) of the last iteration when time_steps was set: out[0] =
- * the whole iteration (graph launch), out[1] = the grouped BSE kernel. */
+ * the whole iteration (graph launch), out[1] = the grouped BSE kernel (0 when
+ * there is none). */
 PQ_API pq_status pq_batch_times(const pq_batch *b, float *out2);
 
 /* Message of the last failure on the batch. */

@@ -1,9 +1,12 @@
 // Batches of independent parquet solves on one GPU (C ABI, include/parquet.h).
 //
 // An iteration of the batch is every member's iteration with the Bethe-Salpeter
-// products (Eq. PA_F_Phi) of all members in ONE persistent grouped launch of the
-// TMA-fed BF16x3 kernel: its problem table lists each member's products with the
-// first tile of each, so small and large solves share the SMs in one schedule.
+// products (Eq. PA_F_Phi) of the small members (n < 512) in ONE persistent grouped launch
+// of the TMA-fed split-precision kernel: its problem table lists each member's products
+// with the first tile of each, so the small solves share the SMs in one schedule.  A
+// member whose matrices fill the GPU alone (n >= 512) runs its products in its own launch
+// right after its other steps, as it does alone: grouping such members measured slower
+// (three n = 576 members: 27.0 ms grouped against 25.2 ms in three launches, same clocks).
 // The whole iteration (members' steps, grouped products, gather of the members'
 // convergence scalars and their device->host copy) is captured once as a CUDA
 // graph and replayed; the members' steps are captured on four branch streams (the members
@@ -37,6 +40,8 @@ struct pq_batch {
   std::vector<std::pair<int, int>> cand;  // candidate (tile index, order) still to time
   bool warmed = false;             // the untimed first iteration that precedes the tuning ran
   std::vector<int> branch;         // branch stream of each member
+  std::vector<char> own;           // the member runs its products in its own launch (n >= kOwnN)
+  int ngroup = 0;                  // members whose products are in the grouped launch
   float tuned[4] = {0, 0, 0, 0};
   int tile = -1, order = -1;       // chosen (indices into tab)
   cudaGraph_t graph = nullptr;
@@ -50,6 +55,7 @@ struct pq_batch {
 namespace {
 
 const int kTileCols[2] = {128, 64};
+const int kOwnN = 512;  // members with n >= kOwnN keep their own product launch
 
 pq_status bfail(pq_batch *b, pq_status s, const char *fmt, ...) {
   char buf[512];
@@ -106,7 +112,7 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph
     pq_ctx *c = b->m[i];
     cudaStream_t keep = c->st;
     c->st = b->br[b->branch[i] % nbr];
-    pq_status s = pq::enqueue_iteration(c, false, false);
+    pq_status s = pq::enqueue_iteration(c, b->own[i] != 0, false);
     c->st = keep;
     if (s != PQ_OK) return bfail(b, s, "member step failed: %s", c->err.c_str());
   }
@@ -115,8 +121,9 @@ pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph
     BCK(cudaStreamWaitEvent(b->st, b->join[j], 0));
   }
   if (timing) BCK(rec(b->ev[1]));
-  BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->m[0]->b.vfmt == pq::V_F16P, b->tab[ti][order], (int)b->m.size(),
-                         b->tiles[ti], b->err, 0));
+  if (b->ngroup > 0)
+    BCK(pq::launch_bse_tma(b->st, kTileCols[ti], b->m[0]->b.vfmt == pq::V_F16P, b->tab[ti][order], b->ngroup,
+                           b->tiles[ti], b->err, 0));
   if (timing) BCK(rec(b->ev[2]));
   const int n = (int)b->m.size();
   gather_kernel<<<(n + 127) / 128, 128, 0, b->st>>>(b->scal, n, b->err, b->gather);
@@ -226,29 +233,35 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
   for (int i = 0; i < count; ++i) sp[i] = ctxs[i]->b.scal;
   if (bad(cudaMemcpy((void *)b->scal, sp.data(), sizeof(double *) * count, cudaMemcpyHostToDevice), "upload"))
     return PQ_ECUDA;
-  // problem tables: members in the given order, or by decreasing matrix size
-  std::vector<int> idx(count);
-  for (int i = 0; i < count; ++i) idx[i] = i;
+  // problem tables of the grouped members: in the given order, or by decreasing matrix size
+  b->own.assign(count, 0);
+  std::vector<int> idx;
+  for (int i = 0; i < count; ++i) {
+    b->own[i] = ctxs[i]->g.n >= kOwnN;
+    if (!b->own[i]) idx.push_back(i);
+  }
+  const int ng = (int)idx.size();
+  b->ngroup = ng;
   std::vector<int> big = idx;
   std::stable_sort(big.begin(), big.end(), [&](int x, int y) { return ctxs[x]->g.n > ctxs[y]->g.n; });
-  for (int ti = 0; ti < 2; ++ti) {
+  for (int ti = 0; ti < 2 && ng > 0; ++ti) {
     for (int od = 0; od < 2; ++od) {
       const std::vector<int> &ord = od ? big : idx;
-      std::vector<pq::BseProblem> t(count);
+      std::vector<pq::BseProblem> t(ng);
       long long tile0 = 0;
-      for (int i = 0; i < count; ++i) {
+      for (int i = 0; i < ng; ++i) {
         t[i] = ctxs[ord[i]]->prob_host;
         t[i].tile0 = tile0;
         tile0 += pq::bse_tiles(kTileCols[ti], t[i].n, t[i].batch);
       }
       b->tiles[ti] = tile0;
-      if (bad(cudaMalloc((void **)&b->tab[ti][od], sizeof(pq::BseProblem) * count), "alloc")) return PQ_ECUDA;
-      if (bad(cudaMemcpy(b->tab[ti][od], t.data(), sizeof(pq::BseProblem) * count, cudaMemcpyHostToDevice),
+      if (bad(cudaMalloc((void **)&b->tab[ti][od], sizeof(pq::BseProblem) * ng), "alloc")) return PQ_ECUDA;
+      if (bad(cudaMemcpy(b->tab[ti][od], t.data(), sizeof(pq::BseProblem) * ng, cudaMemcpyHostToDevice),
               "upload"))
         return PQ_ECUDA;
     }
   }
-  for (int ti = 0; ti < 2; ++ti) {
+  for (int ti = 0; ti < 2 && ng > 0; ++ti) {
     if (o.tile_cols && kTileCols[ti] != o.tile_cols) continue;
     for (int od = 0; od < 2; ++od) {
       if (o.order >= 0 && od != o.order) continue;
@@ -260,13 +273,13 @@ pq_status pq_batch_create(pq_batch **out, pq_ctx *const *ctxs, int count, const 
     b->order = b->cand[0].second;
     b->cand.clear();
   }
-  // branch streams: the members whose matrices fill the GPU (n >= 512) run their steps one
-  // after another on branch 0, where concurrency would only contend for it; the smaller ones
-  // are spread over the other branches, so their short kernels overlap
+  // branch streams: the members whose matrices fill the GPU (n >= kOwnN) run their steps and
+  // their products one after another on branch 0, where concurrency would only contend for
+  // it; the smaller ones are spread over the other branches, so their short kernels overlap
   b->branch.assign(count, 0);
   int next = 0;
   for (int i = 0; i < count; ++i)
-    if (ctxs[i]->g.n < 512) b->branch[i] = 1 + (next++ % 3);
+    if (!b->own[i]) b->branch[i] = 1 + (next++ % 3);
   for (pq_ctx *c : b->m) c->in_batch = true;
   *out = b;
   return PQ_OK;

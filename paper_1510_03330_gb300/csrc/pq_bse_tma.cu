@@ -104,20 +104,31 @@ struct Tile {
   int z, row0, col0, kt;
 };
 
-// Tile t of the launch: the problem whose tile range holds t (binary search on tile0),
-// then GEMM, row block and column block within it (columns fastest).
+// Problems whose first tile and size the CTA keeps in shared memory (a batch with more
+// members searches the table in global memory).  The copies fit in the 1 KB of static
+// shared memory the kernel has anyway: with more, the CTA's shared memory passes the
+// 196 KB carveout, the next one (228 KB) leaves 28 KB of L1 instead of 60, and the
+// products ran 35 % slower.
+constexpr int PMAX = 64;
+
+// Tile t of the launch: the problem whose tile range holds t (binary search on tile0, in the
+// shared copies t0s/ns when nprob <= PMAX), then GEMM, row block and column block within it
+// (columns fastest).  The shared copies keep the search off global memory: the epilogue's
+// reads of Phi evict the table from L1, and every role decodes at every tile boundary.
 template <int BNC>
-__device__ __forceinline__ Tile decode(const BseProblem *__restrict__ probs, int nprob, long long t) {
+__device__ __forceinline__ Tile decode(const BseProblem *__restrict__ probs, const long long *t0s, const int *ns,
+                                       int nprob, long long t) {
+  const bool sh = nprob <= PMAX;
   int lo = 0, hi = nprob - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile0 <= t) lo = mid;
+    if ((sh ? t0s[mid] : probs[mid].tile0) <= t) lo = mid;
     else hi = mid - 1;
   }
   Tile r;
   r.p = probs + lo;
-  const int n = r.p->n, ntc = (n + BNC - 1) / BNC, per_z = ((n + BM - 1) / BM) * ntc;
-  const long long u = t - r.p->tile0;
+  const int n = sh ? ns[lo] : r.p->n, ntc = (n + BNC - 1) / BNC, per_z = ((n + BM - 1) / BM) * ntc;
+  const long long u = t - (sh ? t0s[lo] : r.p->tile0);
   r.z = (int)(u / per_z);
   const int rem = (int)(u % per_z);
   r.row0 = (rem / ntc) * BM;
@@ -138,7 +149,13 @@ __global__ void __maxnreg__(Geo<BNC>::MAXREG)
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tslot;
+  __shared__ long long t0s[PMAX];
+  __shared__ int ns[PMAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < nprob && i < PMAX; i += blockDim.x) {
+    t0s[i] = probs[i].tile0;
+    ns[i] = probs[i].n;
+  }
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
@@ -169,7 +186,7 @@ __global__ void __maxnreg__(Geo<BNC>::MAXREG)
       // ------------------------------------------------------------ TMA producer
       long long it = 0;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const Tile T = decode<BNC>(probs, nprob, t);
+        const Tile T = decode<BNC>(probs, t0s, ns, nprob, t);
         const CUtensorMap *mA = &T.p->mapA, *mB = &T.p->mapB;
         for (int kt = 0; kt < T.kt; ++kt, ++it) {
           const int s = (int)(it % NS);
@@ -201,7 +218,7 @@ __global__ void __maxnreg__(Geo<BNC>::MAXREG)
       long long it = 0, ch = 0;  // stages and accumulator chunks of this CTA
       bool issued = false;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const Tile T = decode<BNC>(probs, nprob, t);
+        const Tile T = decode<BNC>(probs, t0s, ns, nprob, t);
         const int kch = KCH;  // stages per accumulator chunk
         for (int k0 = 0; k0 < T.kt; k0 += kch, ++ch) {
           const int b = (int)(ch & 1);
@@ -285,7 +302,7 @@ __global__ void __maxnreg__(Geo<BNC>::MAXREG)
       mx0 = mx1 = mx2 = mx3 = 0.f;
     };
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-      const Tile T = decode<BNC>(probs, nprob, t);
+      const Tile T = decode<BNC>(probs, t0s, ns, nprob, t);
       if (T.p != mp) {
         flush();
         mp = T.p;

@@ -73,6 +73,40 @@ def test_batch_members_follow_their_own_iteration(tile_cols, order, precision):
 
 
 @pytest.mark.parametrize("precision", list(PLANE))
+def test_batch_large_member_keeps_its_own_products(precision):
+    """A member with n >= 512 runs its products in its own launch inside the batch graph (the
+    grouped launch holds only the small members); every member still follows its own iteration,
+    and a batch of large members only has no grouped launch to tune."""
+    from paper_1510_03330_gb300.binding import Batch, Solver
+
+    big = Params("square", beta=2.0, U=1.0, mu=0.0, L=4, n_nu=32, n_Omega=2)  # n = 512
+    members = [MEMBERS[1], big, MEMBERS[3]]
+    iters = 7
+    alone = [Solver(p, precision=precision) for p in members]
+    for s in alone:
+        s.iterate(iters)
+    mem = [Solver(p, precision=precision) for p in members]
+    with Batch(mem, time_steps=True) as b:
+        for _ in range(iters):
+            d = b.iterate(1)
+        cfg = b.config()
+        t = b.times()
+    assert cfg["tile_cols"] in (64, 128) and t["bse"] > 0, (cfg, t)
+    assert np.all(np.isfinite(d)) and np.all(d > 0)
+    tol, tol_phi = PLANE[precision]
+    for p, a, m in zip(members, alone, mem):
+        assert rel(m.sigma(), a.sigma()) < tol, p
+        assert rel(all_phi(m, p), all_phi(a, p)) < tol_phi, p
+    with Batch([mem[1]]) as b:
+        b.iterate(2)
+        assert b.config()["tile_cols"] == -1
+    alone[1].iterate(2)
+    assert rel(mem[1].sigma(), alone[1].sigma()) < tol
+    for s in alone + mem:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", list(PLANE))
 def test_batch_member_matches_oracle(precision):
     from paper_1510_03330_gb300.binding import Batch, Solver
 
