@@ -106,6 +106,31 @@ def test_batch_large_member_keeps_its_own_products(precision):
         s.close()
 
 
+def test_batch_more_members_than_the_shared_table():
+    """65 grouped members: more than the grouped kernel keeps in shared memory (64), so the
+    CTAs search the problem table in global memory; members at both ends of the table and
+    across the boundary follow their own iteration."""
+    from paper_1510_03330_gb300.binding import Batch, Solver
+
+    tol, tol_phi = PLANE[SPLIT_FP16X3]
+    members = [MEMBERS[i % 2].with_(U=1.0 + 0.01 * i) for i in range(65)]
+    check = [0, 1, 63, 64]
+    iters = 7
+    alone = [Solver(members[i], precision=SPLIT_FP16X3) for i in check]
+    for s in alone:
+        s.iterate(iters)
+    mem = [Solver(p, precision=SPLIT_FP16X3) for p in members]
+    with Batch(mem, tile_cols=128, order=0) as b:
+        d = b.iterate(iters)
+    assert np.all(np.isfinite(d)) and np.all(d > 0)
+    for i, a in zip(check, alone):
+        p = members[i]
+        assert rel(mem[i].sigma(), a.sigma()) < tol, i
+        assert rel(all_phi(mem[i], p), all_phi(a, p)) < tol_phi, i
+    for s in alone + mem:
+        s.close()
+
+
 @pytest.mark.parametrize("precision", list(PLANE))
 def test_batch_member_matches_oracle(precision):
     from paper_1510_03330_gb300.binding import Batch, Solver
