@@ -54,26 +54,44 @@ struct TGeo {
   int tx;     // bytes gathered per step
   int ring_n; // threads per block index a (hb * rows)
   unsigned long long m_per, m_gn, m_nom;  // x / d = (x * m_d) >> 32 for x < 2^16 (d = 3 tiles' copies, G NOmega, NOmega)
+  unsigned long long m_L;                 // the same for d = L (momentum indices x < L^2 < 2^16)
 };
 
 __device__ __forceinline__ int mdiv(int x, unsigned long long m) { return (int)(((unsigned long long)x * m) >> 32); }
+
+// Lattice momentum arithmetic (a + b, -a, a - b on the L x L grid, index x L + y) with the
+// divisions by L done by mdiv: a division by a runtime divisor goes through int <-> float
+// conversions, which run on the narrow FP64 pipe of this part, and the step tables are
+// rebuilt every step while the other warps wait.
+__device__ __forceinline__ int tadd(const Grid &g, const TGeo &t, int a, int b) {
+  const int L = g.L, xa = mdiv(a, t.m_L), xb = mdiv(b, t.m_L);
+  int x = xa + xb, y = (a - xa * L) + (b - xb * L);
+  if (x >= L) x -= L;
+  if (y >= L) y -= L;
+  return x * L + y;
+}
+__device__ __forceinline__ int tneg(const Grid &g, const TGeo &t, int a) {
+  const int L = g.L, x = mdiv(a, t.m_L), y = a - x * L;
+  return (x ? L - x : 0) * L + (y ? L - y : 0);
+}
+__device__ __forceinline__ int tsub(const Grid &g, const TGeo &t, int a, int b) { return tadd(g, t, a, tneg(g, t, b)); }
 
 // Momentum bookkeeping of one step, T_N ints per block b: the transfer groups (and the R
 // column block) its gathers read, and the output rows of the step.  Kept in shared memory so
 // that the lattice additions (integer divisions by L) are done once per block and step.
 enum { T_QR, T_CR, T_QP, T_QS, T_PQK, T_CM, T_Q0, T_N };
 // dm: the gathers of q = qt (the d/m step, or a fused step); else those feeding q' = qt.
-__device__ inline void step_table(const Grid &g, bool dm, int qt, int ik, int p0, int b, int *e) {
+__device__ inline void step_table(const Grid &g, const TGeo &t, bool dm, int qt, int ik, int p0, int b, int *e) {
   const int pb = p0 + b;
-  const int qb_ = dm ? qt : ksub(g, ksub(g, qt, ik), pb);  // q of this block's slices
-  const int x = dm ? kadd(g, kadd(g, ik, pb), qt) : qt;    // q' = k + p_b + q: S group, s/t output row
-  e[T_QR] = ksub(g, pb, ik);
-  e[T_CR] = kadd(g, ik, qb_);
+  const int qb_ = dm ? qt : tsub(g, t, tsub(g, t, qt, ik), pb);  // q of this block's slices
+  const int x = dm ? tadd(g, t, tadd(g, t, ik, pb), qt) : qt;    // q' = k + p_b + q: S group, s/t output row
+  e[T_QR] = tsub(g, t, pb, ik);
+  e[T_CR] = tadd(g, t, ik, qb_);
   e[T_QP] = qb_;
   e[T_QS] = x;
-  e[T_PQK] = ksub(g, x, ik);
-  e[T_CM] = kadd(g, ik, qt);
-  e[T_Q0] = kadd(g, kadd(g, ik, p0), qt);
+  e[T_PQK] = tsub(g, t, x, ik);
+  e[T_CM] = tadd(g, t, ik, qt);
+  e[T_Q0] = tadd(g, t, tadd(g, t, ik, p0), qt);
 }
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
@@ -320,15 +338,16 @@ __global__ void __launch_bounds__(TT, 2)
   const int col0 = p0 * nnu + 4 * cu;  // first output column of this thread: p_a Nnu + npi0
 
   for (int i = tid; i < 2 * G * nom; i += blockDim.x) {
-    const int x = i / (G * nom), b = (i / nom) % G, mt = i % nom;
-    const int Qt = ksub(g, p0 + b, ik) * nom + mt;
+    const int x = mdiv(i, t.m_gn), rem = i - x * G * nom;
+    const int b = mdiv(rem, t.m_nom), mt = rem - b * nom;
+    const int Qt = tsub(g, t, p0 + b, ik) * nom + mt;
     FK[i] = f2(k1[(long long)x * g.nQ + Qt] + k2row[((long long)x * g.n + k) * g.nQ + Qt]);
   }
   const int nsteps = FUSED ? g.nk : 2 * pass.nq;
   // step -> (kind, q): FUSED walks q = 0..nk-1 (both kinds); otherwise target qt, d/m then s/t
   auto step_q = [&](int st) { return FUSED ? st : pass.qb + st / 2; };
   auto step_dm = [&](int st) { return FUSED || (st & 1) == 0; };
-  if (tid < G) step_table(g, step_dm(0), step_q(0), ik, p0, tid, stab[0] + tid * T_N);
+  if (tid < G) step_table(g, t, step_dm(0), step_q(0), ik, p0, tid, stab[0] + tid * T_N);
   if (PF == V_F16P && tid < 8) ssc[tid] = fsc[tid < 4 ? FSC_SA + tid : FSC_SB + tid - 4];
   if (tid == 0) {
     abort_flag = 0;
@@ -345,8 +364,10 @@ __global__ void __launch_bounds__(TT, 2)
   float4 *dl = ring + (size_t)8 * t.ring_n * (a * (a - 1) / 2) + row0 * t.hb + cu % t.hb;
   uint32_t phase = 0;
 
-  int qy = 0;  // FUSED: y coordinate of q (q = step)
-  for (int step = 0; step < nsteps; ++step, qy = (qy + 1 == g.L) ? 0 : qy + 1) {
+  int qy = 0;    // FUSED: y coordinate of q (q = step)
+  int slot = 0;  // FUSED, a > 0: qy % a, this step's delay-line slot
+  for (int step = 0; step < nsteps;
+       ++step, qy = (qy + 1 == g.L) ? 0 : qy + 1, slot = (qy == 0 || slot + 1 == a) ? 0 : slot + 1) {
     const bool do_dm = step_dm(step), do_st = FUSED || !do_dm;
     const int qt = step_q(step);
     const int *tb = stab[step & 1];
@@ -363,7 +384,7 @@ __global__ void __launch_bounds__(TT, 2)
     }
     phase ^= 1u;
     if (tid < G && step + 1 < nsteps)
-      step_table(g, step_dm(step + 1), step_q(step + 1), ik, p0, tid, stab[(step + 1) & 1] + tid * T_N);
+      step_table(g, t, step_dm(step + 1), step_q(step + 1), ik, p0, tid, stab[(step + 1) & 1] + tid * T_N);
 
     float2 sacc = make_float2(0.f, 0.f);  // this step's part of the dF box sum
     for (int mi = row0; worker && mi < nom; mi += t.rows) {
@@ -391,7 +412,7 @@ __global__ void __launch_bounds__(TT, 2)
           // Block 0 of row q0 = k + p_0 + q is produced now; block a >= 1 of that row was
           // produced a steps ago (same lattice row of q) and waits in the delay line.  All
           // blocks of the row are stored by one put4 (one warp instruction per plane).
-          float4 *sl = dl + (size_t)8 * t.ring_n * (a > 0 ? qy % a : 0);
+          float4 *sl = dl + (size_t)8 * t.ring_n * (a > 0 ? slot : 0);
           if (a == 0 || qy >= a) {
             float2 wg[2][4], wf[2][4];
             if (a == 0) {
@@ -466,6 +487,8 @@ constexpr int SMEM_TWO_PER_SM = (228 * 1024) / 2 - 1024 - 4352;
 
 // Tile geometry for G blocks; false if it does not serve the shape.
 bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
+  // the multiply-high divisions (mdiv) are exact for dividends below 2^16
+  if (6 * G * g.n_om >= 65536 || g.L * g.L >= 65536) return false;
   t.G = G;
   t.hb = g.n_nu / 4;
   t.upr = G * t.hb;
@@ -498,6 +521,7 @@ bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   t.m_per = magic(2 * G * g.n_om);
   t.m_gn = magic(G * g.n_om);
   t.m_nom = magic(g.n_om);
+  t.m_L = magic(g.L);
   return t.smem <= 200 * 1024;
 }
 
