@@ -49,7 +49,8 @@ struct TGeo {
   int rows;   // output rows (frequencies m) per sweep
   int nthr;   // blockDim: upr * rows rounded up to whole warps (the copies are issued by a full warp)
   int RS, RA; // row stride and block stride (float2) of the R tiles
-  int PW, BW; // row stride and block stride (float2) of the P and S tiles
+  int PW, BW; // row stride and block stride (float2) of the S tile
+  int PPW;    // row stride (float2) of the P tile, whose blocks are adjacent (block stride Nnu)
   int oR, oP, oS, oFK, oRing, oBar, smem;  // shared-memory layout (bytes)
   int tx;     // bytes gathered per step
   int ring_n; // threads per block index a (hb * rows)
@@ -107,31 +108,48 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 //   R from group p_b - k at column block k + q_b, P from group q_b, S from group qt.
 // P and S take column block p_b.
 __device__ inline void issue_gather(const Grid &g, const TGeo &t, const int *tb, const float2 *phi, int k, int p0,
-                                    float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar) {
+                                    float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar, bool merge) {
   const int G = t.G, nom = g.n_om, nnu = g.n_nu;
   const long long nn = g.n, chan = (long long)g.nQ * nn * nn;
   const uint32_t b = tc::smem_u32(bar);
   if (threadIdx.x == 0) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(t.tx) : "memory");
-  // one copy per (tile, channel, block, transfer row): the blocks of a P or S row sit at a
-  // padded stride in shared memory (bank spread), so they are copied separately
-  const int per = 2 * G * nom;
+  // one copy per (tile, channel, block, transfer row): the blocks of an S row sit at a
+  // padded stride in shared memory (bank spread), so they are copied separately; the G
+  // blocks of a P row are adjacent in the tile and, on d/m steps (merge), come from one
+  // transfer, so they take one copy (the copies, not their bytes, bound the issue).  A warp
+  // issues its lanes' copies one after another, so every warp takes an equal share of
+  // them (consecutive indices, lanes round robin): the gather is issued when the warp with
+  // the most copies is done.
+  const int per = 2 * G * nom, nP = merge ? 2 * nom : per, nall = 2 * per + nP;
   const uint32_t bytes = (uint32_t)nnu * 8u;
-  for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
-    const int tile = mdiv(i, t.m_per), ii = i - tile * per;
-    const int x = mdiv(ii, t.m_gn), rem = ii - x * G * nom;
-    const int a = mdiv(rem, t.m_nom), mt = rem - a * nom;
-    const int *e = tb + a * T_N;
+  const int nw = blockDim.x >> 5, wpc = (nall + nw - 1) / nw, w0 = (threadIdx.x >> 5) * wpc;
+  for (int j = threadIdx.x & 31; j < wpc && w0 + j < nall; j += 32) {
+    const int i = w0 + j;
+    const int tile = i < per ? 0 : (i < per + nP ? 1 : 2);
+    const int ii = i - (tile == 0 ? 0 : (tile == 1 ? per : per + nP));
     const float2 *src;
     float2 *dst;
-    if (tile == 0) {
-      src = phi + x * chan + ((long long)(e[T_QR] * nom + mt) * nn + k) * nn + (long long)e[T_CR] * nnu;
-      dst = Rt + (x * G + a) * t.RA + mt * t.RS;
+    uint32_t nb = bytes;
+    if (tile == 1 && merge) {
+      // the G blocks of a P row are adjacent in Phi and in the tile: one copy
+      const int x = mdiv(ii, t.m_nom), mt = ii - x * nom;
+      src = phi + x * chan + ((long long)(tb[T_QP] * nom + mt) * nn + k) * nn + (long long)p0 * nnu;
+      dst = Pt + (x * nom + mt) * t.PPW;
+      nb = (uint32_t)G * bytes;
     } else {
-      const int qg = tile == 1 ? e[T_QP] : e[T_QS];
-      src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)(p0 + a) * nnu;
-      dst = (tile == 1 ? Pt : St) + (x * nom + mt) * t.PW + a * t.BW;
+      const int x = mdiv(ii, t.m_gn), rem = ii - x * G * nom;
+      const int a = mdiv(rem, t.m_nom), mt = rem - a * nom;
+      const int *e = tb + a * T_N;
+      if (tile == 0) {
+        src = phi + x * chan + ((long long)(e[T_QR] * nom + mt) * nn + k) * nn + (long long)e[T_CR] * nnu;
+        dst = Rt + (x * G + a) * t.RA + mt * t.RS;
+      } else {
+        const int qg = tile == 1 ? e[T_QP] : e[T_QS];
+        src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)(p0 + a) * nnu;
+        dst = tile == 1 ? Pt + (x * nom + mt) * t.PPW + a * nnu : St + (x * nom + mt) * t.PW + a * t.BW;
+      }
     }
-    bulk_load(tc::smem_u32(dst), src, bytes, b);
+    bulk_load(tc::smem_u32(dst), src, nb, b);
   }
 }
 
@@ -215,7 +233,7 @@ __device__ inline float2 f2(double2 v) { return make_float2((float)v.x, (float)v
 // Everything one thread needs to evaluate its four elements of a step.
 struct Ctx {
   const float2 *Rt, *Pt, *St, *FK;
-  int G, RS, RA, PW, BW, nom, nnu, a, npi0, n, mi;
+  int G, RS, RA, PW, BW, PPW, nom, nnu, a, npi0, n, mi;
 };
 
 // map A (column nc = k + q) or C (column nc2 = q' - k') of the R tile of block a, or the fill
@@ -251,8 +269,8 @@ __device__ inline void elems_dm(const Grid &g, const Ctx &c, const Lam &lam, flo
       Bs = c.St[(0 * c.nom + mb - g.m_lo) * c.PW + c.a * c.BW + npi];
       Bt = c.St[(1 * c.nom + mb - g.m_lo) * c.PW + c.a * c.BW + npi];
     }
-    const float2 od = c.Pt[(0 * c.nom + c.mi) * c.PW + c.a * c.BW + npi];
-    const float2 om = c.Pt[(1 * c.nom + c.mi) * c.PW + c.a * c.BW + npi];
+    const float2 od = c.Pt[(0 * c.nom + c.mi) * c.PPW + c.a * c.nnu + npi];
+    const float2 om = c.Pt[(1 * c.nom + c.mi) * c.PPW + c.a * c.nnu + npi];
     const float2 Gd = lam_at<TAB, float2>(lam, 0, l0, m, n, np_) + (-0.5f) * Ad + (-1.5f) * Am + 0.5f * Bs + 1.5f * Bt;
     const float2 Gm = lam_at<TAB, float2>(lam, 1, l1, m, n, np_) + (-0.5f) * Ad + 0.5f * Am + (-0.5f) * Bs + 0.5f * Bt;
     const float2 Fd = Gd + od, Fm = Gm + om;
@@ -281,8 +299,8 @@ __device__ inline void elems_st(const Grid &g, const Ctx &c, const Lam &lam, flo
     float2 Dd = make_float2(0.f, 0.f), Dm = Dd;
     const int md = m - n - np_ - 1;  // transfer q' - k - k' = q of map D
     if (md >= g.m_lo && md <= g.m_hi) {
-      Dd = c.Pt[(0 * c.nom + md - g.m_lo) * c.PW + c.a * c.BW + npi];
-      Dm = c.Pt[(1 * c.nom + md - g.m_lo) * c.PW + c.a * c.BW + npi];
+      Dd = c.Pt[(0 * c.nom + md - g.m_lo) * c.PPW + c.a * c.nnu + npi];
+      Dm = c.Pt[(1 * c.nom + md - g.m_lo) * c.PPW + c.a * c.nnu + npi];
     }
     const float2 os = c.St[(0 * c.nom + c.mi) * c.PW + c.a * c.BW + npi];
     const float2 ot = c.St[(1 * c.nom + c.mi) * c.PW + c.a * c.BW + npi];
@@ -359,7 +377,7 @@ __global__ void __launch_bounds__(TT, 2)
   const float2 l0 = f2(lam.l[0]), l1 = f2(lam.l[1]), l2 = f2(lam.l[2]), l3 = f2(lam.l[3]);
   const float2 twoU = make_float2((float)(2.0 * g.U), 0.f);
   CSum2 acc;  // this thread's dF box sum: a compensated sum of the per-step partial sums
-  Ctx c{Rt, Pt, St, FK, G, t.RS, t.RA, t.PW, t.BW, nom, nnu, a, 4 * (cu % t.hb), n, row0};
+  Ctx c{Rt, Pt, St, FK, G, t.RS, t.RA, t.PW, t.BW, t.PPW, nom, nnu, a, 4 * (cu % t.hb), n, row0};
   // this thread's delay line: a slots of 8 float4 (Gamma X_s, Gamma X_t, F_s, F_t of 4 elements)
   float4 *dl = ring + (size_t)8 * t.ring_n * (a * (a - 1) / 2) + row0 * t.hb + cu % t.hb;
   uint32_t phase = 0;
@@ -371,7 +389,7 @@ __global__ void __launch_bounds__(TT, 2)
     const bool do_dm = step_dm(step), do_st = FUSED || !do_dm;
     const int qt = step_q(step);
     const int *tb = stab[step & 1];
-    issue_gather(g, t, tb, phi, k, p0, Rt, Pt, St, bar);
+    issue_gather(g, t, tb, phi, k, p0, Rt, Pt, St, bar, do_dm);
     if (!tc::mbar_wait_ns(bar, phase, GATHER_WAIT_NS)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
@@ -502,6 +520,7 @@ bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   t.RA = g.n_om * t.RS + 2;
   t.BW = g.n_nu + 2;
   t.PW = G * t.BW;
+  t.PPW = G * g.n_nu + 2;
   t.ring_n = t.hb * t.rows;
   int o = 0;
   t.oR = o;

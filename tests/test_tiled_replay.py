@@ -26,13 +26,14 @@ def geometry(L, nnu, nom, fused):
             return None
         RS, BW = nnu + 2, nnu + 2
         RA, PW = nom * RS + 2, G * BW
+        PPW = G * nnu + 2  # P tile: adjacent blocks, padded rows (allocated at the S tile's stride PW)
         sm = a128(2 * G * RA * 8)
         sm = a128(sm + 2 * nom * PW * 8)
         sm = a128(sm + 2 * nom * PW * 8)
         sm = a128(sm + 2 * G * nom * 8)
         if fused:
             sm = a128(sm + 16 * 8 * hb * rows * (G * (G - 1) // 2))
-        return dict(G=G, hb=hb, upr=upr, rows=rows, RS=RS, RA=RA, BW=BW, PW=PW, smem=sm + 8)
+        return dict(G=G, hb=hb, upr=upr, rows=rows, RS=RS, RA=RA, BW=BW, PW=PW, PPW=PPW, smem=sm + 8)
 
     cands = [c for c in (geo(G) for G in (4, 2, 1) if L % G == 0) if c and c["smem"] <= 200 * 1024]
     if not cands:
@@ -58,7 +59,8 @@ def replay(L, nnu, nom, fused, q_chunk=None):
     c = geometry(L, nnu, nom, fused)
     assert c is not None
     G, hb, upr, rows = c["G"], c["hb"], c["upr"], c["rows"]
-    RS, RA, BW, PW = c["RS"], c["RA"], c["BW"], c["PW"]
+    RS, RA, BW, PW, PPW = c["RS"], c["RA"], c["BW"], c["PW"], c["PPW"]
+    assert PPW <= PW and PPW % 2 == 0
     ring_n = hb * rows
     ring_sz = 8 * ring_n * (G * (G - 1) // 2)
     chan = nQ * n * n
@@ -85,11 +87,26 @@ def replay(L, nnu, nom, fused, q_chunk=None):
                                 assert 0 <= src and src + nnu <= 4 * chan and src % 2 == 0
                                 dst = (x * G + b) * RA + mt * RS
                                 assert dst % 2 == 0 and dst + nnu <= 2 * G * RA
-                                for qg, xo in ((qs_, 0), (xg, 2)):
-                                    src = (x + xo) * chan + ((qg * nom + mt) * n + k) * n + pb * nnu
+                                # S: one copy per block; P: one copy per block on s/t steps
+                                src = (x + 2) * chan + ((xg * nom + mt) * n + k) * n + pb * nnu
+                                assert src + nnu <= 4 * chan and src % 2 == 0
+                                dst = (x * nom + mt) * PW + b * BW
+                                assert dst % 2 == 0 and dst + nnu <= 2 * nom * PW
+                                if not do_dm:
+                                    src = x * chan + ((qs_ * nom + mt) * n + k) * n + pb * nnu
                                     assert src + nnu <= 4 * chan and src % 2 == 0
-                                    dst = (x * nom + mt) * PW + b * BW
-                                    assert dst % 2 == 0 and dst + nnu <= 2 * nom * PW
+                                    dst = (x * nom + mt) * PPW + b * nnu
+                                    assert dst % 2 == 0 and dst + nnu <= (x * nom + mt + 1) * PPW
+                    if do_dm:
+                        # P on d/m steps: the G blocks of a row share their transfer qt and are
+                        # adjacent in Phi and in the tile, so one copy moves the whole row
+                        for mt in range(nom):
+                            for x in range(2):
+                                src = x * chan + ((qt * nom + mt) * n + k) * n + p0 * nnu
+                                assert src + G * nnu <= 4 * chan and src % 2 == 0
+                                assert p0 * nnu + G * nnu <= n  # within one row of Phi
+                                dst = (x * nom + mt) * PPW
+                                assert dst % 2 == 0 and dst + G * nnu <= (x * nom + mt + 1) * PPW
                     for tid in range(upr * rows):
                         cu, row0 = tid % upr, tid // upr
                         a = cu // hb
