@@ -34,6 +34,7 @@
 #include "pq_common.cuh"
 #include "pq_internal.h"
 #include "pq_tc.cuh"
+#include "pq_tma.cuh"
 
 namespace pq {
 
@@ -48,7 +49,8 @@ struct TGeo {
   int upr;    // G * hb: thread columns per output row
   int rows;   // output rows (frequencies m) per sweep
   int nthr;   // blockDim: upr * rows rounded up to whole warps (the copies are issued by a full warp)
-  int RS, RA; // row stride and block stride (float2) of the R tiles
+  int RS, RA; // row stride (= the TMA box width) and block stride (float2) of the R tiles
+  int sh;     // R tile of block a: its Nnu columns start a * sh words into each row
   int PW, BW; // row stride and block stride (float2) of the S tile
   int PPW;    // row stride (float2) of the P tile, whose blocks are adjacent (block stride Nnu)
   int oR, oP, oS, oFK, oRing, oBar, smem;  // shared-memory layout (bytes)
@@ -107,8 +109,9 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 // for the s/t step of q' = qt, with q_b = qt - k - p_b:
 //   R from group p_b - k at column block k + q_b, P from group q_b, S from group qt.
 // P and S take column block p_b.
-__device__ inline void issue_gather(const Grid &g, const TGeo &t, const int *tb, const float2 *phi, int k, int p0,
-                                    float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar, bool merge) {
+__device__ inline void issue_gather(const Grid &g, const TGeo &t, const CUtensorMap *rmap, const int *tb,
+                                    const float2 *phi, int k, int p0, float2 *Rt, float2 *Pt, float2 *St, uint64_t *bar,
+                                    bool merge) {
   const int G = t.G, nom = g.n_om, nnu = g.n_nu;
   const long long nn = g.n, chan = (long long)g.nQ * nn * nn;
   const uint32_t b = tc::smem_u32(bar);
@@ -120,13 +123,22 @@ __device__ inline void issue_gather(const Grid &g, const TGeo &t, const int *tb,
   // issues its lanes' copies one after another, so every warp takes an equal share of
   // them (consecutive indices, lanes round robin): the gather is issued when the warp with
   // the most copies is done.
-  const int per = 2 * G * nom, nP = merge ? 2 * nom : per, nall = 2 * per + nP;
+  const int per = 2 * G * nom, nR = 2 * G, nP = merge ? 2 * nom : per, nall = nR + nP + per;
   const uint32_t bytes = (uint32_t)nnu * 8u;
   const int nw = blockDim.x >> 5, wpc = (nall + nw - 1) / nw, w0 = (threadIdx.x >> 5) * wpc;
   for (int j = threadIdx.x & 31; j < wpc && w0 + j < nall; j += 32) {
     const int i = w0 + j;
-    const int tile = i < per ? 0 : (i < per + nP ? 1 : 2);
-    const int ii = i - (tile == 0 ? 0 : (tile == 1 ? per : per + nP));
+    if (i < nR) {
+      // R of channel x and block a: one tensor box of RS columns x NOmega transfers, started
+      // a * sh columns early so that the block's Nnu columns sit a * sh words into each row
+      const int x = i >= G, a = i - x * G;
+      const int *e = tb + a * T_N;
+      tma::load3(tc::smem_u32(Rt + (x * G + a) * t.RA), rmap, e[T_CR] * nnu - a * t.sh, k,
+                 x * g.nQ + e[T_QR] * nom, bar);
+      continue;
+    }
+    const int tile = i < nR + nP ? 1 : 2;
+    const int ii = i - (tile == 1 ? nR : nR + nP);
     const float2 *src;
     float2 *dst;
     uint32_t nb = bytes;
@@ -140,14 +152,9 @@ __device__ inline void issue_gather(const Grid &g, const TGeo &t, const int *tb,
       const int x = mdiv(ii, t.m_gn), rem = ii - x * G * nom;
       const int a = mdiv(rem, t.m_nom), mt = rem - a * nom;
       const int *e = tb + a * T_N;
-      if (tile == 0) {
-        src = phi + x * chan + ((long long)(e[T_QR] * nom + mt) * nn + k) * nn + (long long)e[T_CR] * nnu;
-        dst = Rt + (x * G + a) * t.RA + mt * t.RS;
-      } else {
-        const int qg = tile == 1 ? e[T_QP] : e[T_QS];
-        src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)(p0 + a) * nnu;
-        dst = tile == 1 ? Pt + (x * nom + mt) * t.PPW + a * nnu : St + (x * nom + mt) * t.PW + a * t.BW;
-      }
+      const int qg = tile == 1 ? e[T_QP] : e[T_QS];
+      src = phi + (x + (tile == 1 ? 0 : 2)) * chan + ((long long)(qg * nom + mt) * nn + k) * nn + (long long)(p0 + a) * nnu;
+      dst = tile == 1 ? Pt + (x * nom + mt) * t.PPW + a * nnu : St + (x * nom + mt) * t.PW + a * t.BW;
     }
     bulk_load(tc::smem_u32(dst), src, nb, b);
   }
@@ -233,7 +240,7 @@ __device__ inline float2 f2(double2 v) { return make_float2((float)v.x, (float)v
 // Everything one thread needs to evaluate its four elements of a step.
 struct Ctx {
   const float2 *Rt, *Pt, *St, *FK;
-  int G, RS, RA, PW, BW, PPW, nom, nnu, a, npi0, n, mi;
+  int G, RS, RA, PW, BW, PPW, nom, nnu, a, npi0, n, mi, ash;
 };
 
 // map A (column nc = k + q) or C (column nc2 = q' - k') of the R tile of block a, or the fill
@@ -242,8 +249,8 @@ __device__ inline void r_at(const Grid &g, const Ctx &c, int ti, bool inT, int c
   vd = vm = make_float2(0.f, 0.f);
   if (!inT) return;
   if (col >= g.n_lo && col <= g.n_hi) {
-    vd = c.Rt[(0 * c.G + c.a) * c.RA + ti * c.RS + col - g.n_lo];
-    vm = c.Rt[(1 * c.G + c.a) * c.RA + ti * c.RS + col - g.n_lo];
+    vd = c.Rt[(0 * c.G + c.a) * c.RA + ti * c.RS + c.ash + col - g.n_lo];
+    vm = c.Rt[(1 * c.G + c.a) * c.RA + ti * c.RS + c.ash + col - g.n_lo];
   } else {
     vd = c.FK[(0 * c.G + c.a) * c.nom + ti];
     vm = c.FK[(1 * c.G + c.a) * c.nom + ti];
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(TT, 2)
                           const double2 *__restrict__ k2row, const float2 *__restrict__ xph,
                           const float2 *__restrict__ xpp, const float2 *__restrict__ gtab,
                           double2 *__restrict__ dfpart, Lam lam, Pass pass, const float *__restrict__ fsc,
-                          int *err) {
+                          int *err, const __grid_constant__ CUtensorMap rmap) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double2 red[TT];
   __shared__ float ssc[8];  // FP16 planes: scales of Gamma X and F per channel
@@ -377,7 +384,7 @@ __global__ void __launch_bounds__(TT, 2)
   const float2 l0 = f2(lam.l[0]), l1 = f2(lam.l[1]), l2 = f2(lam.l[2]), l3 = f2(lam.l[3]);
   const float2 twoU = make_float2((float)(2.0 * g.U), 0.f);
   CSum2 acc;  // this thread's dF box sum: a compensated sum of the per-step partial sums
-  Ctx c{Rt, Pt, St, FK, G, t.RS, t.RA, t.PW, t.BW, t.PPW, nom, nnu, a, 4 * (cu % t.hb), n, row0};
+  Ctx c{Rt, Pt, St, FK, G, t.RS, t.RA, t.PW, t.BW, t.PPW, nom, nnu, a, 4 * (cu % t.hb), n, row0, a * t.sh};
   // this thread's delay line: a slots of 8 float4 (Gamma X_s, Gamma X_t, F_s, F_t of 4 elements)
   float4 *dl = ring + (size_t)8 * t.ring_n * (a * (a - 1) / 2) + row0 * t.hb + cu % t.hb;
   uint32_t phase = 0;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(TT, 2)
     const bool do_dm = step_dm(step), do_st = FUSED || !do_dm;
     const int qt = step_q(step);
     const int *tb = stab[step & 1];
-    issue_gather(g, t, tb, phi, k, p0, Rt, Pt, St, bar, do_dm);
+    issue_gather(g, t, &rmap, tb, phi, k, p0, Rt, Pt, St, bar, do_dm);
     if (!tc::mbar_wait_ns(bar, phase, GATHER_WAIT_NS)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
@@ -500,8 +507,8 @@ __global__ void __launch_bounds__(TT, 2)
 int align128(int x) { return (x + 127) & ~127; }
 
 // Dynamic shared memory of a CTA such that two fit on an SM (228 KB, less 1 KB reserved
-// and the static arrays per CTA).
-constexpr int SMEM_TWO_PER_SM = (228 * 1024) / 2 - 1024 - 4352;
+// and the static arrays per CTA, 4480 bytes with the FP16 scales).
+constexpr int SMEM_TWO_PER_SM = (228 * 1024) / 2 - 1024 - 4480;
 
 // Tile geometry for G blocks; false if it does not serve the shape.
 bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
@@ -516,8 +523,13 @@ bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   t.rows = (g.n_om + sweeps - 1) / sweeps;
   t.nthr = (t.upr * t.rows + 31) / 32 * 32;
   if (fused && t.rows < g.n_om) return false;
-  t.RS = g.n_nu + 2;
-  t.RA = g.n_om * t.RS + 2;
+  if (g.n_om > 256 || g.n_nu + 6 > 256) return false;  // TMA box dimensions
+  // R rows: TMA boxes of Nnu + 2 max(G - 1, 1) words (16-byte multiples, = 2 mod 4 words so
+  // that consecutive transfer rows fall on different banks), block a shifted by 2a words
+  // (bank spread between the blocks); blocks at 128-byte boundaries (TMA destinations)
+  t.sh = G > 1 ? 2 : 0;
+  t.RS = g.n_nu + 2 * std::max(G - 1, 1);
+  t.RA = (g.n_om * t.RS + 15) / 16 * 16;
   t.BW = g.n_nu + 2;
   t.PW = G * t.BW;
   t.PPW = G * g.n_nu + 2;
@@ -526,7 +538,7 @@ bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   t.oR = o;
   o = align128(o + 2 * G * t.RA * 8);
   t.oP = o;
-  o = align128(o + 2 * g.n_om * t.PW * 8);
+  o = align128(o + 2 * g.n_om * t.PPW * 8);
   t.oS = o;
   o = align128(o + 2 * g.n_om * t.PW * 8);
   t.oFK = o;
@@ -535,7 +547,7 @@ bool tiled_geo_g(const Grid &g, bool fused, int G, TGeo &t) {
   if (fused) o = align128(o + 16 * 8 * t.ring_n * (G * (G - 1) / 2));
   t.oBar = o;
   t.smem = o + 8;
-  t.tx = 6 * G * g.n_om * g.n_nu * 8;
+  t.tx = 2 * G * g.n_om * t.RS * 8 + 4 * G * g.n_om * g.n_nu * 8;  // R boxes (whole boxes), P, S
   auto magic = [](unsigned d) { return (unsigned long long)(0xFFFFFFFFull / d) + 1ull; };
   t.m_per = magic(2 * G * g.n_om);
   t.m_gn = magic(G * g.n_om);
@@ -571,9 +583,11 @@ cudaError_t tiled_launch(cudaStream_t st, const Grid &g, const TGeo &t, Buffers 
   auto kfn = assemble_tiled_kernel<FUSED, TAB, PF>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
   if (e != cudaSuccess) return e;
+  CUtensorMap rmap;
+  if (make_phi_rows_map(b.phi, g.n, 4LL * g.nQ, t.RS, g.n_om, &rmap) != CUDA_SUCCESS) return cudaErrorInvalidValue;
   kfn<<<dim3(g.nk / t.G, g.n), t.nthr, t.smem, st>>>(
       g, t, (const float2 *)b.phi, (uint16_t *)b.gam, (uint16_t *)b.fv, ps, b.ld, b.k1, b.k2row, b.xph32, b.xpp32,
-      b.gtab32, b.dfpart, lam, p, b.fsc, (int *)(b.scal + 4));
+      b.gtab32, b.dfpart, lam, p, b.fsc, (int *)(b.scal + 4), rmap);
   return cudaGetLastError();
 }
 

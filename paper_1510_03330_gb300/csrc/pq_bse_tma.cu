@@ -478,6 +478,19 @@ CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long lo
   }
 }
 
+CUresult make_phi_rows_map(const void *phi, int n, long long slabs, int box_w, int box_h, CUtensorMap *map) {
+  const PFN_cuTensorMapEncodeTiled_v12000 cuTensorMapEncodeTiled = tensor_map_encoder();
+  if (!cuTensorMapEncodeTiled) return CUDA_ERROR_NOT_FOUND;
+  // x = k' (contiguous complex64 words), y = k, z = (channel, Q)
+  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)slabs};
+  const cuuint64_t str[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w, 1, (cuuint32_t)box_h};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void *>(phi), dims, str, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 template <int BNC, bool F16>
 static cudaError_t launch_one(cudaStream_t st, unsigned grid, const BseProblem *probs, int nprob, long long tiles,
                               int *err) {

@@ -173,6 +173,9 @@ long long bse_tiles(int bnc, int n, int batch);
 // f16: FP16 planes (four F planes), else BF16 planes (six F planes)
 CUresult make_bse_maps(void *gam_planes, void *fv_planes, int n, int ld, long long slabs, bool f16,
                        CUtensorMap *mapA, CUtensorMap *mapB);
+// Tensor map of complex64 Phi [slabs][n][n] as 8-byte words (x = k', y = k, z = slab), boxes of
+// box_w x 1 x box_h: the parquet assembly's gathers of a column block over box_h transfers.
+CUresult make_phi_rows_map(const void *phi, int n, long long slabs, int box_w, int box_h, CUtensorMap *map);
 // bnc: complex output columns per tile (128 or 64); f16: FP16 operand planes, else BF16;
 // max_ctas > 0 caps the persistent grid
 cudaError_t launch_bse_tma(cudaStream_t st, int bnc, bool f16, const BseProblem *probs, int nprob, long long tiles,

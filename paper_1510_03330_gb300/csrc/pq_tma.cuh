@@ -31,6 +31,13 @@ __device__ __forceinline__ void load4(uint32_t dst, const CUtensorMap *map, int 
       : "memory");
 }
 
+__device__ __forceinline__ void load3(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, void *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 TT = 256
-SMEM_TWO_PER_SM = (228 * 1024) // 2 - 1024 - 4352
+SMEM_TWO_PER_SM = (228 * 1024) // 2 - 1024 - 4480
 
 
 def geometry(L, nnu, nom, fused):
@@ -24,16 +24,21 @@ def geometry(L, nnu, nom, fused):
         rows = (nom + sweeps - 1) // sweeps
         if fused and rows < nom:
             return None
-        RS, BW = nnu + 2, nnu + 2
-        RA, PW = nom * RS + 2, G * BW
-        PPW = G * nnu + 2  # P tile: adjacent blocks, padded rows (allocated at the S tile's stride PW)
+        if nom > 256 or nnu + 6 > 256:
+            return None
+        sh = 2 if G > 1 else 0        # R block a starts a * sh words into its rows
+        RS = nnu + 2 * max(G - 1, 1)  # R rows = TMA box width
+        RA = (nom * RS + 15) // 16 * 16
+        BW = nnu + 2
+        PW = G * BW
+        PPW = G * nnu + 2  # P tile: adjacent blocks, padded rows
         sm = a128(2 * G * RA * 8)
-        sm = a128(sm + 2 * nom * PW * 8)
+        sm = a128(sm + 2 * nom * PPW * 8)
         sm = a128(sm + 2 * nom * PW * 8)
         sm = a128(sm + 2 * G * nom * 8)
         if fused:
             sm = a128(sm + 16 * 8 * hb * rows * (G * (G - 1) // 2))
-        return dict(G=G, hb=hb, upr=upr, rows=rows, RS=RS, RA=RA, BW=BW, PW=PW, PPW=PPW, smem=sm + 8)
+        return dict(G=G, hb=hb, upr=upr, rows=rows, RS=RS, RA=RA, BW=BW, PW=PW, PPW=PPW, sh=sh, smem=sm + 8)
 
     cands = [c for c in (geo(G) for G in (4, 2, 1) if L % G == 0) if c and c["smem"] <= 200 * 1024]
     if not cands:
@@ -59,8 +64,8 @@ def replay(L, nnu, nom, fused, q_chunk=None):
     c = geometry(L, nnu, nom, fused)
     assert c is not None
     G, hb, upr, rows = c["G"], c["hb"], c["upr"], c["rows"]
-    RS, RA, BW, PW, PPW = c["RS"], c["RA"], c["BW"], c["PW"], c["PPW"]
-    assert PPW <= PW and PPW % 2 == 0
+    RS, RA, BW, PW, PPW, sh = c["RS"], c["RA"], c["BW"], c["PW"], c["PPW"], c["sh"]
+    assert PPW <= PW and PPW % 2 == 0 and RS % 2 == 0 and RS % 4 == 2 and RA % 16 == 0
     ring_n = hb * rows
     ring_sz = 8 * ring_n * (G * (G - 1) // 2)
     chan = nQ * n * n
@@ -81,12 +86,19 @@ def replay(L, nnu, nom, fused, q_chunk=None):
                         pb = p0 + b
                         qs_ = qt if do_dm else ksub(ksub(qt, ik), pb)
                         xg = kadd(kadd(ik, pb), qt) if do_dm else qt
+                        for x in range(2):
+                            # R: one TMA box (x0 .. x0 + RS, row k, slabs z .. z + nom) of the
+                            # channel-x Phi viewed as [4 nQ][n][n]; its Nnu columns start b*sh in
+                            x0 = kadd(ik, qs_) * nnu - b * sh
+                            z = x * nQ + ksub(pb, ik) * nom
+                            assert x0 % 2 == 0  # 16-byte aligned innermost coordinate
+                            assert 0 <= x0 + b * sh and x0 + b * sh + nnu <= n  # the wanted columns
+                            assert 0 <= z and z + nom <= 4 * nQ and 0 <= k < n
+                            dst = (x * G + b) * RA
+                            assert dst % 16 == 0 and dst + nom * RS <= 2 * G * RA  # 128-byte aligned
+                            assert b * sh + nnu <= RS
                         for mt in range(nom):
                             for x in range(2):
-                                src = x * chan + ((ksub(pb, ik) * nom + mt) * n + k) * n + kadd(ik, qs_) * nnu
-                                assert 0 <= src and src + nnu <= 4 * chan and src % 2 == 0
-                                dst = (x * G + b) * RA + mt * RS
-                                assert dst % 2 == 0 and dst + nnu <= 2 * G * RA
                                 # S: one copy per block; P: one copy per block on s/t steps
                                 src = (x + 2) * chan + ((xg * nom + mt) * n + k) * n + pb * nnu
                                 assert src + nnu <= 4 * chan and src % 2 == 0
