@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pq_assemble.cuh"
 #include "pq_ctx.h"
 #include "pq_tc.cuh"
@@ -178,7 +180,20 @@ pq_status find_mu(pq_ctx *c, double target, double *mu_out) {
 // its grouped launch); timing records the step events.
 }  // namespace
 
+namespace pq {
+// Named host range (NVTX) around the enqueue of one step group, so that a profiler's timeline
+// (or ncu --nvtx-include "pq.assemble/") ties the kernels to the steps of the iteration.  The
+// calls cost nothing when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace pq
+
 pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
+  NvtxRange whole("pq.iteration");
   cudaStream_t st = c->st;
   Grid &g = c->g;
   Buffers &b = c->b;
@@ -194,20 +209,29 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
     g.mu = mu;
   }
   mark(0);
-  CK(pq::launch_tail_and_green(st, g, b));
-  mark(1);
-  CK(pq::launch_bubbles(st, g, b));
-  if (b.vfmt == pq::V_F16P) CK(pq::launch_split_scales(st, b, c->lam_max));
-  mark(2);
-  CK(pq::launch_kernels_extract(st, g, b, c->c64, pq::split_planes(b.vfmt) && c->krow_ok));
+  {
+    NvtxRange r("pq.one_body");
+    CK(pq::launch_tail_and_green(st, g, b));
+    mark(1);
+    CK(pq::launch_bubbles(st, g, b));
+    if (b.vfmt == pq::V_F16P) CK(pq::launch_split_scales(st, b, c->lam_max));
+    mark(2);
+  }
+  {
+    NvtxRange r("pq.kernels");
+    CK(pq::launch_kernels_extract(st, g, b, c->c64, pq::split_planes(b.vfmt) && c->krow_ok));
+  }
   mark(3);
-  if (b.truncated) {
-    mark(4);
-    CK(pq::launch_sigma_truncated(st, g, b));
-  } else {
-    CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
-    mark(4);
-    CK(pq::launch_sigma2(st, g, c->z, b));
+  {
+    NvtxRange r("pq.sigma");
+    if (b.truncated) {
+      mark(4);
+      CK(pq::launch_sigma_truncated(st, g, b));
+    } else {
+      CK(pq::launch_sigma1(st, g, c->z, pq::sigma1_args(b, b.sigma, b.scal, b.sigma1)));
+      mark(4);
+      CK(pq::launch_sigma2(st, g, c->z, b));
+    }
   }
   mark(5);
   const long long nn = g.n;
@@ -223,8 +247,11 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
     const int zc = p.nq * g.n_om;
     const long long q0 = (long long)p.qb * g.n_om;
     if (tm && !fused) cudaEventRecord(c->pev[3 * ip], st);
-    CK(pq::launch_assemble(st, g, b, c->lam, p));
-    if (!fused) CK(pq::launch_chi(st, g, b, p.qb, p.nq));
+    {
+      NvtxRange r("pq.assemble");
+      CK(pq::launch_assemble(st, g, b, c->lam, p));
+      if (!fused) CK(pq::launch_chi(st, g, b, p.qb, p.nq));
+    }
     if (fused) {
       mark(6);
       CK(pq::launch_sigma_update(st, g, b));
@@ -235,6 +262,7 @@ pq_status pq::enqueue_iteration(pq_ctx *c, bool bse, bool timing) {
     void *phi_out = fused ? b.phi : b.phi_new;
     if (pq::split_planes(b.vfmt) && ip == 0)  // the products of this iteration sum the new Phi's row edges
       CK(cudaMemsetAsync(b.krow, 0, sizeof(double2) * 4 * (size_t)g.n * g.nQ, st));
+    NvtxRange rb("pq.bse");
     if (!bse) {
       // left to the caller
     } else if (pq::split_planes(b.vfmt)) {

@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pq_ctx.h"
 
 struct pq_batch {
@@ -100,6 +102,10 @@ float elapsed(cudaEvent_t a, cudaEvent_t z) {
 // In a graph capture the timing events become record nodes of the graph (external records);
 // a plain record during capture would only order work inside the capture.
 pq_status enqueue_all(pq_batch *b, int ti, int order, bool timing, bool in_graph = false) {
+  nvtxRangePushA("pq.batch_iteration");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   auto rec = [&](cudaEvent_t e) {
     return in_graph ? cudaEventRecordWithFlags(e, b->st, cudaEventRecordExternal) : cudaEventRecord(e, b->st);
   };
