@@ -146,7 +146,7 @@ def test_split_tf32x3_iterations_match_oracle(name):
 
 # Tolerances of the plane formats on the small shapes (max-norm relative error of Sigma, F and
 # chi; of the raw product Phi, whose k''-sums cancel, in the second entry): FP16x3 keeps 2^-22
-# per product and its accumulation in chunks, the benchmark spec's bound of 1e-6; BF16x3 keeps
+# per product and its accumulation in chunks, the split path's bound of 1e-6; BF16x3 keeps
 # 2^-16 per product, which is not averaged down at these sizes (measured up to 2.3e-6 on F).
 PLANE_TOL = {"split_fp16x3": (TOL_SPLIT, 2 * TOL_SPLIT), "split_bf16x3": (5 * TOL_SPLIT, 1.5e-5)}
 
@@ -218,7 +218,7 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
     # n = 1024 with TF32 pieces: one FP32 accumulator per tile over the whole k range (the
     # kernel of the complex64 operands), measured bounds above the 1e-6 target for F and Phi
     ("square8_u2_b4", "split_tf32x3", TOL_SPLIT, 5 * TOL_SPLIT, 15 * TOL_SPLIT),
-    # FP16 planes, chunked accumulation: the benchmark spec's bound on Sigma, F and chi, every channel.
+    # FP16 planes, chunked accumulation: the 1e-6 bound on Sigma, F and chi, every channel.
     # The raw product Phi of the second iteration is a small difference of large k''-terms
     # built from the complex64 (FP32) assembly: its error, ~3.7e-6 of the vertex scale, is
     # that rounding amplified by the cancellation, not the products' (BF16x3 4.2e-6, TF32x3
