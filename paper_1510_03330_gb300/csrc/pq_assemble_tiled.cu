@@ -6,10 +6,10 @@
 // operand row is written in runs of G * Nnu contiguous columns instead of Nnu.
 //
 // One CTA per (row leg k, group of G k'-momenta p_a = p_0 + a that are consecutive in one
-// lattice row, G | L).  Per q-momentum step it gathers with bulk copies (one mbarrier):
-//   R_x[a] = Phi_x[(p_a - k, .)][k][(k + q, .)]      x = d, m   (maps A and C)
-//   P_x    = Phi_x[(q, .)][k][(p_0 .. p_G-1, .)]      x = d, m   (own d/m, map D)
-//   S_x[a] = Phi_x[(k + p_a + q, .)][k][(p_a, .)]     x = s, t   (map B, own s/t)
+// lattice row, G | L).  Per q-momentum step it gathers, completing on one mbarrier:
+//   R_x[a] = Phi_x[(p_a - k, .)][k][(k + q, .)]      x = d, m   (maps A and C; a TMA box each)
+//   P_x    = Phi_x[(q, .)][k][(p_0 .. p_G-1, .)]      x = d, m   (own d/m, map D; a bulk copy per row)
+//   S_x[a] = Phi_x[(k + p_a + q, .)][k][(p_a, .)]     x = s, t   (map B, own s/t; a bulk copy per row)
 // and each thread computes four consecutive k' of one output row (one frequency m).
 //
 // The d/m outputs of a step fill rows (q, m) over all G blocks.  The s/t outputs of block a
