@@ -22,6 +22,8 @@ SHAPES = {
     "bethe_nu12": Params("bethe", beta=4.0, U=1.0, mu=0.0, L=1, n_nu=12, n_Omega=9),  # nk = 1
     "L4_nu16": Params("square", beta=4.0, U=2.0, mu=0.0, L=4, n_nu=16, n_Omega=16),  # the bench block shape
     "L4_nu4": Params("square", beta=3.0, U=1.5, mu=0.1, L=4, n_nu=4, n_Omega=4),     # G = 4 at oracle-friendly size
+    "L4_nu24": Params("square", beta=3.0, U=1.2, mu=0.2, L=4, n_nu=24, n_Omega=6),   # 30-word R boxes, 6 row threads
+    "L2_nu32": Params("square", beta=2.5, U=1.0, mu=0.0, L=2, n_nu=32, n_Omega=9),   # G = 2, 34-word boxes, odd NOmega
 }
 
 
@@ -46,7 +48,8 @@ def all_phi(s, p):
 
 @pytest.mark.parametrize("precision", list(PLANE))
 @pytest.mark.parametrize("name,q_chunk", [("L4_nu8", 0), ("L4_nu8", 3), ("L2_nu8", 0), ("L3_nu8", 0),
-                                          ("L3_nu8", 4), ("bethe_nu12", 0), ("L4_nu16", 0)])
+                                          ("L3_nu8", 4), ("bethe_nu12", 0), ("L4_nu16", 0), ("L4_nu24", 0),
+                                          ("L4_nu24", 2), ("L2_nu32", 0)])
 def test_tiled_matches_general(name, q_chunk, precision):
     from paper_1510_03330_gb300.binding import Solver
 

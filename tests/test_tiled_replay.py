@@ -159,6 +159,8 @@ def replay(L, nnu, nom, fused, q_chunk=None):
     (1, 12, 9, True, None),   # Bethe (one momentum)
     (4, 8, 8, False, 3),      # two-gather passes, ragged last pass
     (2, 24, 24, False, 3),    # Nnu = 24: G chosen by the shared-memory budget, two row sweeps
+    (4, 24, 6, True, None),   # 30-word R boxes, 24 threads per row
+    (2, 32, 9, True, None),   # Nnu = 32: 34-word R boxes, odd NOmega
 ])
 def test_tiled_schedule_in_bounds_and_exactly_once(L, nnu, nom, fused, q_chunk):
     replay(L, nnu, nom, fused, q_chunk)
