@@ -590,11 +590,8 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
       tau[p * o.tau_order + i] = p * h + 0.5 * h * (gx[i] + 1.0);
       wt[p * o.tau_order + i] = 0.5 * h * gw[i];
     }
-  std::vector<std::complex<double>> E((size_t)2 * z.M * z.ntau), Ef((size_t)z.ntau * g.n_ext);
-  for (int i = 0; i < 2 * z.M; ++i) {
-    double nu = (2.0 * (i - z.M) + 1.0) * M_PI / beta;
-    for (int j = 0; j < z.ntau; ++j) E[(size_t)i * z.ntau + j] = std::exp(std::complex<double>(0.0, -nu * tau[j]));
-  }
+  // E (2M x N_tau complex exponentials) is built on the device from tau; the small tables here
+  std::vector<std::complex<double>> Ef((size_t)z.ntau * g.n_ext);
   for (int j = 0; j < z.ntau; ++j)
     for (int e = 0; e < g.n_ext; ++e) {
       double nu = (2.0 * (g.e_lo + e) + 1.0) * M_PI / beta;
@@ -612,11 +609,13 @@ pq_status pq_init(pq_ctx **out, int lattice, double beta, double U, double mu, i
     if (s == PQ_OK && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       s = fail(c, PQ_ECUDA, "upload failed: %s", cudaGetErrorString(cudaGetLastError()));
   };
-  up(b.s1_E, E.data(), E.size() * cs);
   up(b.s1_Ef, Ef.data(), Ef.size() * cs);
   up(b.s1_ph, ph.data(), ph.size() * cs);
   up(b.s1_phc, phc.data(), phc.size() * cs);
   up(b.s1_tau, tau.data(), tau.size() * sizeof(double));
+  if (s == PQ_OK && (pq::launch_e_table(0, (double2 *)b.s1_E, b.s1_tau, 2 * z.M, z.ntau, beta) != cudaSuccess ||
+                     cudaStreamSynchronize(0) != cudaSuccess))
+    s = fail(c, PQ_ECUDA, "transform table: %s", cudaGetErrorString(cudaGetLastError()));
   if (s == PQ_OK) {
     cudaError_t e1 = cudaMemset(b.phi, 0, vb);
     cudaError_t e2 = cudaMemset(b.sigma, 0, cs * g.nk * g.n_ext);

@@ -123,6 +123,8 @@ cudaError_t launch_split_scales(cudaStream_t st, Buffers &b, const double *lam_m
 cudaError_t launch_sigma1(cudaStream_t st, const Grid &g, const Sizes &z, const Sigma1Args &a);
 Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *out);
 cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1);
+// E[a][j] = exp(-i nu_a tau[j]) for the 2M fermionic frequencies nu_a = (2 (a - M) + 1) pi / beta
+cudaError_t launch_e_table(cudaStream_t st, double2 *E, const double *tau, int two_m, int ntau, double beta);
 // density per site and d density / d mu of G[sigma] at g.mu (square lattice), Matsubara cut M,
 // written to out2[0..1] (zeroed first); c1: device scalar of sigma's 1/(i nu) tail
 cudaError_t launch_density(cudaStream_t st, const Grid &g, int M, const double2 *sigma, const double *c1,

@@ -484,6 +484,26 @@ Sigma1Args sigma1_args(Buffers &b, const double2 *sigma, double *c1, double2 *ou
   return a;
 }
 
+// E[a][j] = exp(-i nu_a tau_j), nu_a = (2 (a - M) + 1) pi / beta for a in [0, 2M): the Matsubara-
+// to-imaginary-time transform of Sigma~1 (tau_j the quadrature nodes), computed where it is used
+// instead of on the host (4 M x N_tau complex exponentials).
+__global__ void e_table_kernel(double2 *E, const double *tau, int two_m, int ntau, double beta) {
+  const long long total = (long long)two_m * ntau;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i / ntau), j = (int)(i - (long long)a * ntau);
+    const double nu = (2.0 * (a - two_m / 2) + 1.0) * CUDART_PI / beta;
+    double sn, cs;
+    sincos(-nu * tau[j], &sn, &cs);
+    E[i] = make_double2(cs, sn);
+  }
+}
+
+cudaError_t launch_e_table(cudaStream_t st, double2 *E, const double *tau, int two_m, int ntau, double beta) {
+  e_table_kernel<<<1216, 256, 0, st>>>(E, tau, two_m, ntau, beta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tail_c1(cudaStream_t st, const Grid &g, const double2 *sigma, double *c1) {
   tail_c1_kernel<<<1, 256, 0, st>>>(g, sigma, c1);
   return cudaGetLastError();
