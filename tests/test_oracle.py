@@ -455,6 +455,29 @@ def _vertex_correction(p):
     return O.sigma2_kernel_terms(g, G, K) + O.sigma_delta_F(g, G, F, K, O.lambda0(p.U))
 
 
+@pytest.mark.parametrize("p", [
+    Params("bethe", beta=5.0, U=1.0, mu=0.0, L=1, n_nu=8, n_Omega=7, mix=1.0),
+    Params("square", beta=2.5, U=1.0, mu=0.4, L=2, n_nu=6, n_Omega=5, mix=1.0),
+])
+def test_vertex_changes_by_one_order_per_iteration(p):
+    """Undamped iteration from Phi = 0 (Sec. II, the perturbative start): the first iterate has
+    F = Lambda0 (order U), the second adds the s U X U Phi's (exactly order U^2), the third the
+    next order (U^3).  So (F2 - F1) / U^2 is the same at every U and (F3 - F2) / U^3 tends to a
+    constant as U -> 0; a term entering at the wrong order breaks one of the two."""
+    r2, r3 = [], []
+    for U in (0.2, 0.1, 0.05):
+        q = p.with_(U=U)
+        st, F = O.zero_state(q), []
+        for _ in range(3):
+            res = O.iterate(q, st)
+            st = res.state
+            F.append(res.F)
+        r2.append(np.abs(F[1] - F[0]).max() / U**2)
+        r3.append(np.abs(F[2] - F[1]).max() / U**3)
+    assert max(r2) / min(r2) < 1 + 1e-9
+    assert max(r3) / min(r3) < 1.02
+
+
 def test_third_order_cancels_in_the_symmetric_impurity_problem():
     """Sigma - Sigma^(2)[G] comes from the order-U^2 Phi's in F.  In the
     particle-hole symmetric single-site problem the third-order self-energy
