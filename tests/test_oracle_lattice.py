@@ -175,6 +175,43 @@ def test_crossing_symmetry_with_flux(flux, p):
     assert checked > p.n_Q * p.n
 
 
+@pytest.mark.parametrize("p", [P3, P3_EVEN])
+def test_spin_rotation_crossing_with_flux(flux, p):
+    """SU(2) symmetry with the exchange of the two outgoing legs (the ph <-> ph-bar crossing,
+    transfer q <-> k' - k), after three iterations with the inversion-breaking flux:
+      F_d(k, k'; q) = -F_d(k, k+q; k'-k)/2 - 3 F_m(k, k+q; k'-k)/2,
+      F_m(k, k'; q) = -F_d(k, k+q; k'-k)/2 +   F_m(k, k+q; k'-k)/2,
+    wherever k+q and k'-k are in the box.  It is not one of the printed crossing relations:
+    the parquet equations produce it through maps A and C and the d/m coefficients, so a wrong
+    leg or transfer there, or a wrong coefficient of Phi_d, Phi_m in Gamma_d, Gamma_m, breaks it.
+    The partner arguments are computed here."""
+    res = iterated(p, 3)
+    g = O.make_grid(p)
+    F = res.F
+    scale = np.abs(F).max()
+    kk, kn, qk, qm = O.box_indices(g)
+    where = {(int(kk[i]), int(kn[i])): i for i in range(p.n)}
+    checked = 0
+    for Q in range(p.n_Q):
+        qx, qy = coords(p, qk[Q])
+        for k in range(p.n):
+            kx, ky = coords(p, kk[k])
+            kq = where.get((idx(p, kx + qx, ky + qy), int(kn[k] + qm[Q])))
+            if kq is None:
+                continue
+            for kp in range(p.n):
+                px, py = coords(p, kk[kp])
+                m = int(kn[kp] - kn[k])
+                if not g.m_lo <= m <= g.m_hi:
+                    continue
+                Q2 = idx(p, px - kx, py - ky) * p.n_Omega + m - g.m_lo
+                fd, fm = F[0, Q2, k, kq], F[1, Q2, k, kq]
+                assert abs(F[0, Q, k, kp] - (-0.5 * fd - 1.5 * fm)) < 1e-13 * scale
+                assert abs(F[1, Q, k, kp] - (-0.5 * fd + 0.5 * fm)) < 1e-13 * scale
+                checked += 1
+    assert checked > p.n_Q * p.n
+
+
 def test_pauli_principle_with_flux(flux):
     """F_t odd and F_s even under k' -> q - k' at transfer frequency 0 (App. A), with
     q - k' computed here: a slip in the momentum of a crossed leg breaks it."""
