@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import parquet_oracle as O
-from paper_1510_03330_gb300.workloads import CONFIGS, Params, random_state
+from paper_1510_03330_gb300.workloads import CONFIGS, SPLIT_FP16X3, Params, random_state
 
 pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-10
@@ -211,6 +211,47 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
             v += O.sigma_delta_F(g, G, Fr, K, lam, ks=[kr])[ik, n - g.e_lo]
         sig_new[(ik, n)] = v
     return phi_new, F, sig_new, s1, X_ph, X_pp
+
+
+@pytest.mark.gpu
+def test_full_size_vertex_keeps_spin_rotation_crossing():
+    """The 8x8 workload at full size (n = 1024, FP16x3, the launch configuration bench.py
+    times), after three iterations: F satisfies the ph <-> ph-bar crossing of SU(2) symmetry,
+      F_d(k, k+d; q) = -F_d(k, k+q; d)/2 - 3 F_m(k, k+q; d)/2,  F_m(k, k+d; q) = -F_d/2 + F_m/2,
+    for every k of two sampled transfers q whose shifted arguments stay in the box, with one
+    shift d, so that all partners lie in the one slice d.  A property of the exact solution at
+    any size; here it holds to the split path's accuracy."""
+    from paper_1510_03330_gb300.binding import Solver
+
+    p = CONFIGS["square8_u2_b4"]
+    g = O.make_grid(p)
+    kk, kn, qk, qm = O.box_indices(g)
+    L, nom = p.L, p.n_Omega
+    where = {(int(kk[i]), int(kn[i])): i for i in range(p.n)}
+    dq, dm = L * 1 + 2, 1                       # shift d = (momentum (1, 2), bosonic frequency 1)
+    Qd = dq * nom + dm - g.m_lo
+    Qs = [3 * nom + 0 - g.m_lo, 37 * nom + 2 - g.m_lo]
+    with Solver(p, precision=SPLIT_FP16X3) as s:
+        s.iterate(3)
+        Fd = [s.F(r, Qd) for r in (0, 1)]
+        FQ = {Q: [s.F(r, Q) for r in (0, 1)] for Q in Qs}
+    scale = max(np.abs(f).max() for f in Fd + [x for v in FQ.values() for x in v])
+    checked, worst = 0, 0.0
+    for Q in Qs:
+        qx, qy = divmod(int(qk[Q]), L)
+        for k in range(p.n):
+            kx, ky = divmod(int(kk[k]), L)
+            kq = where.get((((kx + qx) % L) * L + (ky + qy) % L, int(kn[k] + qm[Q])))
+            kd = where.get((((kx + dq // L) % L) * L + (ky + dq % L) % L, int(kn[k] + dm)))
+            if kq is None or kd is None:
+                continue
+            rd = FQ[Q][0][k, kd] - (-0.5 * Fd[0][k, kq] - 1.5 * Fd[1][k, kq])
+            rm = FQ[Q][1][k, kd] - (-0.5 * Fd[0][k, kq] + 0.5 * Fd[1][k, kq])
+            worst = max(worst, abs(rd), abs(rm))
+            checked += 1
+    print("spin-rotation crossing, full size:", checked, worst / scale)
+    assert checked > p.n
+    assert worst <= 5 * TOL_SPLIT * scale
 
 
 @pytest.mark.parametrize("name,precision,tol,tol_F,tol_phi", [
