@@ -216,7 +216,8 @@ def _oracle_sampled_iteration(p, phi, sigma, Qs, outs):
 @pytest.mark.gpu
 def test_full_size_vertex_keeps_spin_rotation_crossing():
     """The 8x8 workload at full size (n = 1024, FP16x3, the launch configuration bench.py
-    times), after three iterations: F satisfies the ph <-> ph-bar crossing of SU(2) symmetry,
+    times), after three iterations: F satisfies the crossing relations (App. A) and the ph <->
+    ph-bar crossing of SU(2) symmetry,
       F_d(k, k+d; q) = -F_d(k, k+q; d)/2 - 3 F_m(k, k+q; d)/2,  F_m(k, k+d; q) = -F_d/2 + F_m/2,
     for every k of two sampled transfers q whose shifted arguments stay in the box, with one
     shift d, so that all partners lie in the one slice d.  A property of the exact solution at
@@ -231,10 +232,16 @@ def test_full_size_vertex_keeps_spin_rotation_crossing():
     dq, dm = L * 1 + 2, 1                       # shift d = (momentum (1, 2), bosonic frequency 1)
     Qd = dq * nom + dm - g.m_lo
     Qs = [3 * nom + 0 - g.m_lo, 37 * nom + 2 - g.m_lo]
+    # the printed crossing F_d(k, k'; q) = F_s(k, k'; k+k'+q)/2 + 3 F_t(k, k'; k+k'+q)/2 on the
+    # pairs with k + k' = c: all partners in the one slice c + q
+    cq, cn = L * 3 + 5, -1                    # c = (momentum (3, 5), frequencies n + n' = -1)
+    Qc = (((3 + divmod(int(qk[Qs[0]]), L)[0]) % L) * L + (5 + divmod(int(qk[Qs[0]]), L)[1]) % L) * nom \
+        + cn + int(qm[Qs[0]]) + 1 - g.m_lo
     with Solver(p, precision=SPLIT_FP16X3) as s:
         s.iterate(3)
         Fd = [s.F(r, Qd) for r in (0, 1)]
         FQ = {Q: [s.F(r, Q) for r in (0, 1)] for Q in Qs}
+        Fst = [s.F(r, Qc) for r in (2, 3)]
     scale = max(np.abs(f).max() for f in Fd + [x for v in FQ.values() for x in v])
     checked, worst = 0, 0.0
     for Q in Qs:
@@ -252,6 +259,20 @@ def test_full_size_vertex_keeps_spin_rotation_crossing():
     print("spin-rotation crossing, full size:", checked, worst / scale)
     assert checked > p.n
     assert worst <= 5 * TOL_SPLIT * scale
+    Q0, checked, worst = Qs[0], 0, 0.0
+    scale2 = max(scale, max(np.abs(f).max() for f in Fst))
+    for k in range(p.n):
+        kx, ky = divmod(int(kk[k]), L)
+        kp = where.get((((cq // L - kx) % L) * L + (cq % L - ky) % L, cn - int(kn[k])))
+        if kp is None:
+            continue
+        r1 = FQ[Q0][0][k, kp] - (0.5 * Fst[0][k, kp] + 1.5 * Fst[1][k, kp])
+        r2 = FQ[Q0][1][k, kp] - (-0.5 * Fst[0][k, kp] + 0.5 * Fst[1][k, kp])
+        worst = max(worst, abs(r1), abs(r2))
+        checked += 1
+    print("pp-ph crossing, full size:", checked, worst / scale2)
+    assert checked >= p.n // 2
+    assert worst <= 5 * TOL_SPLIT * scale2
 
 
 @pytest.mark.parametrize("name,precision,tol,tol_F,tol_phi", [
